@@ -1,0 +1,18 @@
+"""CPU oracle for the 3D C2C DFT (test infrastructure; see ``oracle.direct_dft``).
+
+Only ``tests/``, ``__graft_entry__.smoke()`` and ``bench.py``'s CPU-baseline
+and reference legs may import this package.  The CUDA library never does.
+"""
+
+from .direct_dft import (  # noqa: F401
+    BACKWARD,
+    FORWARD,
+    backward,
+    dft3,
+    dft3_at,
+    dft3_bruteforce,
+    dft_along_axis,
+    dft_matrix,
+    forward,
+    rel_l2,
+)
