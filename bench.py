@@ -1,0 +1,383 @@
+#!/usr/bin/env python3
+"""Benchmark: 3D C2C FFT (forward + backward) of a 256^3 PME-shaped complex64 grid.
+
+One step = one forward and one backward transform of the whole grid through
+the C ABI (libcroft.so), i.e. every pass of the hot path.  Metric: GFLOP/s with
+the nominal count 5 N log2 N per direction.
+
+Timing: plan outside the timed region; W warm-up steps; then K steps, each
+preceded by an L2 flush (a write of a buffer twice the L2 size, outside the
+timed events); each transform is bracketed by CUDA events on the stream it runs
+on and the step time is the sum of the two.  The dominant pass kernel is timed
+by the plan's own per-pass events inside the same steps.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl croft|reference]
+
+With N > 1 (torchrun) every rank runs an independent replica of the workload
+(the single-grid transform has no data-parallel shard on one box) and value is
+the sum over ranks; the time is the max over ranks.
+
+--impl reference times the FP64 CPU oracle (the only reference this method has)
+on the host cores, on a bounded sample of the same workload.
+"""
+
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+SHAPE = (256, 256, 256)
+WORKLOAD = "pme256: 256x256x256 complex64 C2C forward+backward, 200k +-1 charges spread by order-4 B-splines, seed 1"
+METRIC = "3D C2C FFT GFLOP/s (5N log2 N), % of HBM roofline, TC vs FP32 at fixed error"
+HBM_FALLBACK_GBS = 6800.0
+
+
+def nominal_flops(shape) -> float:
+    n = math.prod(shape)
+    return 5.0 * n * math.log2(n)
+
+
+def measured_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(p) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    except Exception:  # noqa: BLE001
+        return HBM_FALLBACK_GBS, "fallback"
+
+
+def kernel_source_sha() -> str:
+    h = hashlib.sha256()
+    csrc = os.path.join(ROOT, "paper_2002_04896_gb300", "csrc")
+    for name in sorted(os.listdir(csrc)):
+        with open(os.path.join(csrc, name), "rb") as f:
+            h.update(name.encode())
+            h.update(f.read())
+    return h.hexdigest()[:16]
+
+
+def ncu_traffic(kernel_key: str):
+    """DRAM bytes per launch from the committed ncu summary, if it was taken on the current kernel source."""
+    p = os.path.join(ROOT, "profiles", "ncu_dram_traffic.json")
+    try:
+        with open(p) as f:
+            d = json.load(f)
+    except Exception:  # noqa: BLE001
+        return None
+    ent = d.get(kernel_key)
+    if not ent or ent.get("src_sha") != kernel_source_sha():
+        return None
+    return float(ent["dram_bytes_per_launch"])
+
+
+class ClockSampler:
+    """nvidia-smi clocks / throttle reasons sampled every 200 ms while active."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.lines = []
+        self.thread = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "200"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except Exception:  # noqa: BLE001
+            self.proc = None
+            return
+        self.thread = threading.Thread(target=self._read, daemon=True)
+        self.thread.start()
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:  # noqa: BLE001
+            self.proc.kill()
+        if self.thread:
+            self.thread.join(timeout=2)
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax.append(float(parts[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[5:9]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def dist_env():
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return world, rank, local
+
+
+def cpu_oracle_step(x, sample_planes=None):
+    """Forward + backward with the FP64 oracle; optionally on a sample of the pencils of each axis.
+
+    sample_planes = s: the z and y passes run on x-slabs [0, s) and the x pass on
+    y-slabs [0, s): s/nx of the 1D DFTs of every axis (a bounded sample of the step).
+    Returns the nominal flops the sample covers.
+    """
+    import numpy as np
+
+    import oracle
+
+    if sample_planes is None:
+        y = oracle.forward(x)
+        oracle.backward(y.astype(np.complex64))
+        return 2 * nominal_flops(x.shape)
+    s = sample_planes
+    frac = s / x.shape[0]
+    for sign in (oracle.FORWARD, oracle.BACKWARD):
+        a = x[:s].astype(np.complex128)
+        a = oracle.dft_along_axis(a, 2, sign)
+        a = oracle.dft_along_axis(a, 1, sign)
+        b = x[:, :s].astype(np.complex128)
+        oracle.dft_along_axis(b, 0, sign)
+    return 2 * nominal_flops(x.shape) * frac
+
+
+def run_reference(args):
+    world, rank, _ = dist_env()
+    if rank != 0:
+        return 0
+    import numpy as np
+
+    import synthetic_inputs as S
+
+    x = S.config_input("pme256")
+    cores = os.cpu_count()
+    # the whole step unless (steps + warmup) full steps would exceed ~3 minutes; then a
+    # fixed fraction of the pencils of every axis per step
+    t0 = time.perf_counter()
+    cpu_oracle_step(x, None)
+    t_full = time.perf_counter() - t0
+    sample = None
+    if t_full * (args.steps + args.warmup) > 180.0:
+        sample = max(1, int(SHAPE[0] * 180.0 / (t_full * (args.steps + args.warmup))))
+    for _ in range(args.warmup - 1):
+        cpu_oracle_step(x, sample)
+    t0 = time.perf_counter()
+    fl = 0.0
+    for _ in range(args.steps):
+        fl += cpu_oracle_step(x, sample)
+    dt = time.perf_counter() - t0
+    val = fl / dt / 1e9
+    part = "all" if sample is None else f"{sample}/{SHAPE[0]}"
+    desc = (f"FP64 oracle (numpy matmul per-axis DFT), forward+backward on {part} of the pencils "
+            f"of each axis of the pme256 grid per step")
+    line = {
+        "impl": "reference", "metric": METRIC, "value": val, "unit": "GFLOP/s", "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": dt / args.steps * 1e3,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic", "config": {"workload": WORKLOAD, "grid": list(SHAPE)},
+        "cpu_baseline": {"value": val, "unit": "GFLOP/s", "cores": cores, "kind": "oracle", "sample": desc},
+        "e2e": {"value": val, "unit": "GFLOP/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def run_croft(args):
+    import numpy as np
+    import torch
+
+    import synthetic_inputs as S
+    from paper_2002_04896_gb300 import build as _build
+
+    _build.ensure_built()
+    from paper_2002_04896_gb300 import croft
+
+    world, rank, local = dist_env()
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+
+    x_h = S.config_input("pme256")
+    shape = x_h.shape
+    n_total = math.prod(shape)
+    flops_step = 2 * nominal_flops(shape)
+    stream = torch.cuda.Stream(device=dev)
+    x = torch.from_numpy(x_h).to(dev)
+    y = torch.empty_like(x)
+    z = torch.empty_like(x)
+    l2 = torch.cuda.get_device_properties(dev).L2_cache_size
+    flush = torch.empty(max(2 * l2, 256 << 20) // 4, dtype=torch.float32, device=dev)
+
+    plan = croft.Plan(*shape)
+    croft.croft_plan_set_timing(plan.handle, True)
+    launches_per_step = 2 * croft.croft_plan_num_launches(plan.handle)
+    sh = stream.cuda_stream
+
+    def step(record):
+        with torch.cuda.stream(stream):
+            flush.fill_(1.0)
+            e = [torch.cuda.Event(enable_timing=True) for _ in range(4)]
+            e[0].record(stream)
+            croft.croft_exec_forward(plan.handle, x, y, sh)
+            e[1].record(stream)
+        pf = croft.croft_plan_pass_times(plan.handle)
+        with torch.cuda.stream(stream):
+            e[2].record(stream)
+            croft.croft_exec_backward(plan.handle, y, z, sh)
+            e[3].record(stream)
+        pb = croft.croft_plan_pass_times(plan.handle)
+        stream.synchronize()
+        if record is not None:
+            record.append((e[0].elapsed_time(e[1]) + e[2].elapsed_time(e[3]), pf, pb))
+
+    for _ in range(args.warmup):
+        step(None)
+    if world > 1:
+        torch.distributed.barrier()
+    torch.cuda.synchronize()
+    clocks = ClockSampler(torch.cuda.current_device())
+    clocks.start()
+    rec = []
+    t_wall = time.perf_counter()
+    for _ in range(args.steps):
+        step(rec)
+    torch.cuda.synchronize()
+    t_wall = time.perf_counter() - t_wall
+    clk = clocks.stop()
+    ms_total = sum(r[0] for r in rec)
+    if world > 1:
+        t = torch.tensor([ms_total], device=dev)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        ms_total = float(t.item())
+        torch.distributed.barrier()
+    ms_step = ms_total / args.steps
+    value = world * flops_step / (ms_step * 1e-3) / 1e9
+
+    # per-pass kernel times (forward and backward run the same kernels)
+    npass = len(rec[0][1])
+    pass_ms = [statistics.mean([r[1][i] for r in rec] + [r[2][i] for r in rec]) for i in range(npass)]
+    dom = max(range(npass), key=lambda i: pass_ms[i])
+    axis_names = ["z", "y", "x"][-npass:] if npass == 3 else [f"p{i}" for i in range(npass)]
+    peak, peak_kind = measured_peaks()
+    alg_bytes = 16.0 * n_total  # one read + one write of the grid per pass launch
+    achieved = alg_bytes / (pass_ms[dom] * 1e-3) / 1e9
+    dom_key = f"pass_{axis_names[dom]}_{'x'.join(map(str, shape))}"
+    traffic = ncu_traffic(dom_key)
+
+    # end to end through the C ABI with host buffers: H2D of the input, fwd, bwd, D2H of the result
+    x_pin = torch.from_numpy(x_h).pin_memory()
+    z_pin = torch.empty_like(x_pin).pin_memory()
+    e2e = []
+    for i in range(args.warmup + args.steps):
+        with torch.cuda.stream(stream):
+            flush.fill_(1.0)
+            a = torch.cuda.Event(enable_timing=True)
+            b = torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            x.copy_(x_pin, non_blocking=True)
+            croft.croft_exec_forward(plan.handle, x, y, sh)
+            croft.croft_exec_backward(plan.handle, y, z, sh)
+            z_pin.copy_(z, non_blocking=True)
+            b.record(stream)
+        stream.synchronize()
+        if i >= args.warmup:
+            e2e.append(a.elapsed_time(b))
+    e2e_ms = statistics.mean(e2e)
+    if world > 1:
+        t = torch.tensor([e2e_ms], device=dev)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        e2e_ms = float(t.item())
+    e2e_val = world * flops_step / (e2e_ms * 1e-3) / 1e9
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        # whole forward+backward steps of the oracle, repeated for >= 10 s (at most 30 s)
+        t0 = time.perf_counter()
+        fl, reps = 0.0, 0
+        while True:
+            fl += cpu_oracle_step(x_h, None)
+            reps += 1
+            dt = time.perf_counter() - t0
+            if dt >= 10.0 or dt * (reps + 1) / reps > 30.0:
+                break
+        cpu = {"value": fl / dt / 1e9, "unit": "GFLOP/s", "cores": os.cpu_count(), "kind": "oracle",
+               "sample": f"FP64 oracle (numpy matmul per-axis DFT), {reps} full forward+backward step(s) of the "
+                         f"pme256 grid in {dt:.1f} s"}
+
+    plan.close()
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": "GFLOP/s", "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "grid": list(shape), "direction": "forward+backward",
+                       "l2": "flushed before every step (write of a 2x L2 buffer, outside the timed events)",
+                       "parallelism": f"replicas x{world}" if world > 1 else "single GPU",
+                       "passes_per_direction": npass},
+            "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                         "frac": achieved / peak, "traffic": traffic, "kernel": dom_key,
+                         "peak_source": peak_kind, "alg_bytes_per_launch": alg_bytes,
+                         "pass_ms": pass_ms},
+            "hbm_frac_whole_transform": (16.0 * n_total * 2 / (ms_step * 1e-3) / 1e9) / peak,
+            "cpu_baseline": cpu,
+            "e2e": {"value": e2e_val, "unit": "GFLOP/s", "h2d_bytes_per_step": 8 * n_total,
+                    "d2h_bytes_per_step": 8 * n_total, "ms_per_step": e2e_ms},
+            "gpu_launches": launches_per_step * args.steps,
+            "clocks": clk,
+            "wall_s_timed_region": t_wall,
+        }
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        torch.distributed.destroy_process_group()
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="croft", choices=["croft", "reference"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        args.warmup = 3
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_croft(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -1,0 +1,150 @@
+/*
+ * croft.h - C ABI of the GB300 3D complex-to-complex FFT library (libcroft.so).
+ *
+ * The operation (paper Sec. 2.1):
+ *   forward,  Eq. (1): Y(k) = sum_j X(j) exp(-2 pi i (kx jx/Nx + ky jy/Ny + kz jz/Nz))
+ *   backward, Eq. (2): the same sum with exponent sign +.  Eq. (2) prints a
+ *             1/(Nx Ny Nz) factor; this library does NOT apply it (both
+ *             directions unnormalised, so backward(forward(X)) = Nx*Ny*Nz * X).
+ * computed as the paper's row-column method (Sec. 4.1, steps 1-9): batched 1D
+ * FFTs along each axis with the data rearrangement between axes fused into the
+ * FFT passes, and the result returned in the input layout (Sec. 4.2, last
+ * sentence).
+ *
+ * Data layout (every entry point): a grid of shape (nx, ny, nz) in C order, z
+ * contiguous (stride 1), y with stride nz, x with stride ny*nz; elements are
+ * complex64 stored as interleaved {float re, float im} (8 bytes).
+ *
+ * Pointers named `in` / `out` are DEVICE pointers (cudaMalloc, torch CUDA
+ * tensors, ...) owned by the caller, 16-byte aligned.  `in == out` (in place)
+ * is allowed; any other overlap of the two ranges is rejected.  `in` is not
+ * modified unless it equals `out`.
+ *
+ * Streams are passed as `void*` holding a cudaStream_t (NULL = the legacy
+ * default stream).  Execution is asynchronous and stream-ordered: no exec call
+ * synchronises the device.  Launch failures are returned as CROFT_ERR_CUDA.
+ *
+ * Thread safety: distinct plans may be used concurrently from any threads and
+ * streams.  One plan may have at most one exec in flight at a time.
+ *
+ * There is no CPU fallback: without a usable sm_103 device plan creation
+ * fails with CROFT_ERR_CUDA.
+ */
+#ifndef CROFT_H_
+#define CROFT_H_
+
+#include <stddef.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct croft_plan_s* croft_plan; /* opaque, owned by the library */
+
+typedef enum {
+    CROFT_C2C_F32 = 0,           /* complex64 in/out, FP32 CUDA-core butterflies */
+    CROFT_C2C_F32_TC_BF16X3 = 1  /* complex64 in/out, radix-16 stages on tensor cores
+                                    (split bf16 hi+lo operands, FP32 accumulate) */
+} croft_dtype;
+
+typedef enum {
+    CROFT_OK = 0,
+    CROFT_ERR_INVALID_ARG = 1,       /* null/misaligned pointer, partial overlap, bad enum */
+    CROFT_ERR_UNSUPPORTED_SIZE = 2,  /* an axis outside 1..4096 or not of the form 2^a 3^b 5^c */
+    CROFT_ERR_OOM = 3,               /* a device or host allocation failed */
+    CROFT_ERR_CUDA = 4,              /* CUDA runtime error (no device, launch failure, ...) */
+    CROFT_ERR_TIMEOUT = 5            /* a bounded device-side wait gave up (batched form) */
+} croft_status;
+
+/* Human-readable name of a status code (static string, never NULL). */
+const char* croft_status_string(croft_status s);
+
+/*
+ * croft_plan_create - plan a single (nx, ny, nz) transform on the current device.
+ *
+ * Paper: the single reusable 1D plan covering all pencils ("option 4",
+ * Sec. 5.1) and the three-axis schedule of Sec. 4.1.  Factorises each axis
+ * into radix 16/8/4/2/3/5 stages, builds twiddle tables
+ * w = exp(-2 pi i r/n) in float64 with exact integer reduction of r and rounds
+ * them to float32, and uploads them.
+ *
+ *   out   : receives the plan (set to NULL on failure).
+ *   nx,ny,nz : axis lengths, each 1..4096 and 2^a 3^b 5^c.  A length-1 axis
+ *           is the identity.
+ *   dtype : CROFT_C2C_F32 or CROFT_C2C_F32_TC_BF16X3.
+ * Returns CROFT_OK, CROFT_ERR_INVALID_ARG (out NULL, bad dtype),
+ * CROFT_ERR_UNSUPPORTED_SIZE, CROFT_ERR_OOM or CROFT_ERR_CUDA.
+ * The environment variable CROFT_LOG=1 prints the chosen schedule to stderr.
+ */
+croft_status croft_plan_create(croft_plan* out, int nx, int ny, int nz, croft_dtype dtype);
+
+/*
+ * croft_exec_forward - Eq. (1), unnormalised, out = F(in).
+ * croft_exec_backward - Eq. (2) with exponent +, WITHOUT the 1/N factor.
+ *
+ *   plan : from croft_plan_create.
+ *   in, out : device pointers to nx*ny*nz complex64 (layout above).
+ *   stream : cudaStream_t or NULL.
+ * Returns CROFT_OK, CROFT_ERR_INVALID_ARG (NULL plan/pointer, pointer not
+ * 16-byte aligned, partial overlap of in/out) or CROFT_ERR_CUDA.
+ */
+croft_status croft_exec_forward(croft_plan plan, const void* in, void* out, void* stream);
+croft_status croft_exec_backward(croft_plan plan, const void* in, void* out, void* stream);
+
+/* Device scratch bytes held by the plan (0 when every pass runs in place). */
+size_t croft_plan_workspace_bytes(croft_plan plan);
+
+/* Number of kernel launches one exec of this plan issues. */
+int croft_plan_num_launches(croft_plan plan);
+
+/*
+ * croft_plan_describe - write a one-line description of the schedule (axes,
+ * radix order, tile shape and launch shape of every pass) into buf (always
+ * NUL-terminated when cap > 0).  Returns the length the full text needs.
+ */
+int croft_plan_describe(croft_plan plan, char* buf, int cap);
+
+/*
+ * Per-pass timing (tracing hook).  When enabled, each exec records a CUDA
+ * event on the exec stream before the first pass and after every pass.
+ * croft_plan_pass_times waits for the last exec's events and writes the
+ * duration in milliseconds of each pass into ms[0 .. min(cap, passes)-1];
+ * it returns the number of passes timed, 0 when timing is off or no exec ran,
+ * or -1 on a CUDA error.
+ */
+croft_status croft_plan_set_timing(croft_plan plan, int enable);
+int croft_plan_pass_times(croft_plan plan, float* ms, int cap);
+
+/*
+ * Status written by bounded device-side waits during the last exec of this
+ * plan (CROFT_OK or CROFT_ERR_TIMEOUT).  Synchronises with the plan's last
+ * exec.  Plans without device-side waits always return CROFT_OK.
+ */
+croft_status croft_plan_last_device_status(croft_plan plan);
+
+/* Release a plan and its device tables.  NULL is a no-op returning CROFT_OK.
+ * Synchronises with any exec of the plan still in flight. */
+croft_status croft_plan_destroy(croft_plan plan);
+
+/*
+ * Host-side planning helpers (no device needed; used by the tests).
+ *
+ * croft_factorize - the radix schedule the library uses for a length-n axis,
+ * in execution order.  Writes up to cap radices and returns how many stages
+ * there are, or -1 if n is unsupported.
+ *
+ * croft_twiddle_table - the float32 twiddle table for a length-n axis and
+ * the given radix schedule (as returned by croft_factorize): for the stage
+ * with radix R whose input sub-transforms have length p (the product of the
+ * earlier radices), entry p-1 + (j-1)*p + k holds exp(-2 pi i j k/(p R)) for
+ * j = 1..R-1, k = 0..p-1.  Writes 2*(n-1) floats (re, im interleaved).
+ * Returns n-1, or -1 on bad arguments.
+ */
+int croft_factorize(int n, int* radices, int cap);
+int croft_twiddle_table(int n, const int* radices, int nstages, float* out);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* CROFT_H_ */

@@ -1,0 +1,224 @@
+"""Thin ctypes binding of libcroft.so (C ABI in include/croft.h).
+
+Function names match the C entry points.  Arguments are marshalled only:
+device pointers come from torch CUDA tensors (``tensor.data_ptr()``), streams
+from ``torch.cuda.Stream.cuda_stream``; every step of the transform runs in the
+library's CUDA kernels.  There is no fallback: if the shared library is missing
+or fails to load, importing this module raises.
+"""
+
+from __future__ import annotations
+
+import ctypes
+import os
+
+_LIB_PATH = os.path.join(os.path.dirname(os.path.abspath(__file__)), "libcroft.so")
+if not os.path.exists(_LIB_PATH):
+    raise ImportError(f"libcroft.so not built ({_LIB_PATH}); run paper_2002_04896_gb300.build.build()")
+_lib = ctypes.CDLL(_LIB_PATH)
+
+CROFT_C2C_F32 = 0
+CROFT_C2C_F32_TC_BF16X3 = 1
+
+CROFT_OK = 0
+CROFT_ERR_INVALID_ARG = 1
+CROFT_ERR_UNSUPPORTED_SIZE = 2
+CROFT_ERR_OOM = 3
+CROFT_ERR_CUDA = 4
+CROFT_ERR_TIMEOUT = 5
+
+_P = ctypes.c_void_p
+_I = ctypes.c_int
+
+
+def _sig(name, res, args):
+    f = getattr(_lib, name)
+    f.restype = res
+    f.argtypes = args
+    return f
+
+
+_status_string = _sig("croft_status_string", ctypes.c_char_p, [_I])
+_plan_create = _sig("croft_plan_create", _I, [ctypes.POINTER(_P), _I, _I, _I, _I])
+_exec_forward = _sig("croft_exec_forward", _I, [_P, _P, _P, _P])
+_exec_backward = _sig("croft_exec_backward", _I, [_P, _P, _P, _P])
+_workspace_bytes = _sig("croft_plan_workspace_bytes", ctypes.c_size_t, [_P])
+_num_launches = _sig("croft_plan_num_launches", _I, [_P])
+_describe = _sig("croft_plan_describe", _I, [_P, ctypes.c_char_p, _I])
+_set_timing = _sig("croft_plan_set_timing", _I, [_P, _I])
+_pass_times = _sig("croft_plan_pass_times", _I, [_P, ctypes.POINTER(ctypes.c_float), _I])
+_last_device_status = _sig("croft_plan_last_device_status", _I, [_P])
+_plan_destroy = _sig("croft_plan_destroy", _I, [_P])
+_factorize = _sig("croft_factorize", _I, [_I, ctypes.POINTER(_I), _I])
+_twiddle_table = _sig("croft_twiddle_table", _I, [_I, ctypes.POINTER(_I), _I, ctypes.POINTER(ctypes.c_float)])
+
+LIBRARY_PATH = _LIB_PATH
+EXPORTED = [
+    "croft_status_string", "croft_plan_create", "croft_exec_forward", "croft_exec_backward",
+    "croft_plan_workspace_bytes", "croft_plan_num_launches", "croft_plan_describe", "croft_plan_set_timing",
+    "croft_plan_pass_times", "croft_plan_last_device_status", "croft_plan_destroy", "croft_factorize",
+    "croft_twiddle_table",
+]
+
+
+class CroftError(RuntimeError):
+    def __init__(self, status: int, what: str):
+        super().__init__(f"{what}: {croft_status_string(status)}")
+        self.status = status
+
+
+def _check(status: int, what: str) -> None:
+    if status != CROFT_OK:
+        raise CroftError(status, what)
+
+
+def croft_status_string(status: int) -> str:
+    return _status_string(int(status)).decode()
+
+
+def _stream_ptr(stream) -> int:
+    if stream is None:
+        try:
+            import torch
+            return torch.cuda.current_stream().cuda_stream
+        except Exception:  # noqa: BLE001
+            return 0
+    if isinstance(stream, int):
+        return stream
+    return int(stream.cuda_stream)
+
+
+def _ptr(x) -> int:
+    if isinstance(x, int):
+        return x
+    return int(x.data_ptr())
+
+
+# ---------------------------------------------------------------------------
+# raw entry points (status codes returned, not raised)
+# ---------------------------------------------------------------------------
+
+def croft_plan_create_status(nx: int, ny: int, nz: int, dtype: int = CROFT_C2C_F32):
+    h = _P()
+    st = _plan_create(ctypes.byref(h), int(nx), int(ny), int(nz), int(dtype))
+    return st, h.value
+
+
+def croft_exec_forward_status(plan: int, inp, out, stream=None) -> int:
+    return _exec_forward(plan, _ptr(inp), _ptr(out), _stream_ptr(stream))
+
+
+def croft_exec_backward_status(plan: int, inp, out, stream=None) -> int:
+    return _exec_backward(plan, _ptr(inp), _ptr(out), _stream_ptr(stream))
+
+
+# ---------------------------------------------------------------------------
+# raising wrappers with the C names
+# ---------------------------------------------------------------------------
+
+def croft_plan_create(nx: int, ny: int, nz: int, dtype: int = CROFT_C2C_F32) -> int:
+    st, h = croft_plan_create_status(nx, ny, nz, dtype)
+    _check(st, f"croft_plan_create({nx},{ny},{nz},{dtype})")
+    return h
+
+
+def croft_exec_forward(plan: int, inp, out, stream=None) -> None:
+    _check(croft_exec_forward_status(plan, inp, out, stream), "croft_exec_forward")
+
+
+def croft_exec_backward(plan: int, inp, out, stream=None) -> None:
+    _check(croft_exec_backward_status(plan, inp, out, stream), "croft_exec_backward")
+
+
+def croft_plan_workspace_bytes(plan: int) -> int:
+    return int(_workspace_bytes(plan))
+
+
+def croft_plan_num_launches(plan: int) -> int:
+    return int(_num_launches(plan))
+
+
+def croft_plan_describe(plan: int) -> str:
+    need = _describe(plan, None, 0)
+    buf = ctypes.create_string_buffer(max(1, need + 1))
+    _describe(plan, buf, len(buf))
+    return buf.value.decode()
+
+
+def croft_plan_set_timing(plan: int, enable: bool) -> None:
+    _check(_set_timing(plan, 1 if enable else 0), "croft_plan_set_timing")
+
+
+def croft_plan_pass_times(plan: int, cap: int = 8):
+    arr = (ctypes.c_float * cap)()
+    n = _pass_times(plan, arr, cap)
+    if n < 0:
+        raise CroftError(CROFT_ERR_CUDA, "croft_plan_pass_times")
+    return [float(arr[i]) for i in range(min(n, cap))]
+
+
+def croft_plan_last_device_status(plan: int) -> int:
+    return int(_last_device_status(plan))
+
+
+def croft_plan_destroy(plan) -> None:
+    _check(_plan_destroy(plan), "croft_plan_destroy")
+
+
+def croft_factorize(n: int):
+    arr = (_I * 16)()
+    k = _factorize(int(n), arr, 16)
+    return None if k < 0 else [int(arr[i]) for i in range(k)]
+
+
+def croft_twiddle_table(n: int, radices):
+    import numpy as np
+    rad = (_I * max(1, len(radices)))(*radices)
+    out = np.zeros(2 * max(1, n - 1), dtype=np.float32)
+    k = _twiddle_table(int(n), rad, len(radices), out.ctypes.data_as(ctypes.POINTER(ctypes.c_float)))
+    if k < 0:
+        return None
+    return out[: 2 * k].view(np.complex64)
+
+
+class Plan:
+    """RAII helper around a croft plan (torch tensors in, torch tensors out)."""
+
+    def __init__(self, nx: int, ny: int, nz: int, dtype: int = CROFT_C2C_F32):
+        self.shape = (int(nx), int(ny), int(nz))
+        self.dtype = dtype
+        self.handle = croft_plan_create(nx, ny, nz, dtype)
+
+    def forward(self, inp, out=None, stream=None):
+        if out is None:
+            import torch
+            out = torch.empty_like(inp)
+        croft_exec_forward(self.handle, inp, out, stream)
+        return out
+
+    def backward(self, inp, out=None, stream=None):
+        if out is None:
+            import torch
+            out = torch.empty_like(inp)
+        croft_exec_backward(self.handle, inp, out, stream)
+        return out
+
+    def describe(self) -> str:
+        return croft_plan_describe(self.handle)
+
+    def close(self):
+        if self.handle:
+            croft_plan_destroy(self.handle)
+            self.handle = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:  # noqa: BLE001
+            pass

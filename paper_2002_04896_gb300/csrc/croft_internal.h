@@ -1,0 +1,50 @@
+// croft_internal.h - descriptors shared by the planner (host) and the pass kernels.
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "croft_sched.h"
+
+namespace croft {
+
+// How the pencils of one pass sit in memory.
+//  ROW: pencil g occupies elements [g*n, g*n + n)  (the contiguous z axis).
+//  COL: pencil g = b*M + m has element a at b*n*M + a*M + m (a strided axis;
+//       consecutive pencils are consecutive in memory, so a CTA that takes W
+//       consecutive pencils reads W-wide contiguous rows of the tile).
+enum PassLayout { LAYOUT_ROW = 0, LAYOUT_COL = 1 };
+
+// One pass = one batched 1D FFT over every pencil of one axis (one kernel launch).
+struct PassArgs {
+    const float2* tw;   // device twiddle table of the axis, n-1 entries
+    long long M;        // COL: pencils per batch row (= element stride of the axis); ROW: 1
+    long long ncols;    // number of pencils
+    int n;              // FFT length (the kernel is specialised on it; kept for dispatch)
+    int W;              // pencils per CTA
+    int tw_pad;         // float2 slots reserved for twiddles in shared memory
+    float isign;        // +1 forward, -1 backward (conj-in / conj-out)
+};
+
+struct PassLaunch {
+    PassArgs args;
+    int layout;
+    int T;              // threads per pencil (fixed by the kernel: croft_threads_per_pencil)
+    int grid;
+    int block;
+    int smem;           // dynamic shared memory bytes
+};
+
+typedef void (*pass_fn)(const float2*, float2*, const PassArgs);
+
+// croft_kernels.cu, one per size group
+pass_fn lookup_pass_kernel_group_0(int layout, int n);
+pass_fn lookup_pass_kernel_group_1(int layout, int n);
+pass_fn lookup_pass_kernel_group_2(int layout, int n);
+pass_fn lookup_pass_kernel_group_3(int layout, int n);
+
+// croft_passes.cu
+pass_fn pass_kernel_for(int layout, int n);
+cudaError_t prepare_pass(const PassLaunch& L);  // once per plan: opt in to > 48 KB shared memory
+cudaError_t launch_pass(const PassLaunch& L, const float2* in, float2* out, cudaStream_t s);
+
+}  // namespace croft

@@ -1,0 +1,25 @@
+// croft_kernels.cu - instantiates the pass kernel for one group of axis lengths.
+// Compiled once per group (-DCROFT_GROUP=0..3) so the instantiations build in parallel.
+#include "croft_pass_kernel.cuh"
+#include "croft_sizes.h"
+
+#ifndef CROFT_GROUP
+#error "compile with -DCROFT_GROUP=<0..3>"
+#endif
+
+#define CROFT_CAT_(a, b) a##b
+#define CROFT_CAT(a, b) CROFT_CAT_(a, b)
+
+namespace croft {
+
+pass_fn CROFT_CAT(lookup_pass_kernel_group_, CROFT_GROUP)(int layout, int n) {
+#define CROFT_CASE(N) \
+    case N: return layout == LAYOUT_ROW ? croft_pass_kernel<LAYOUT_ROW, N> : croft_pass_kernel<LAYOUT_COL, N>;
+    switch (n) {
+        CROFT_CAT(CROFT_SIZES_, CROFT_GROUP)(CROFT_CASE)
+        default: return nullptr;
+    }
+#undef CROFT_CASE
+}
+
+}  // namespace croft

@@ -1,0 +1,355 @@
+// croft_plan.cu - planner, twiddle tables and the C ABI entry points (include/croft.h).
+//
+// A plan is the GPU counterpart of the paper's single reusable 1D FFT plan that
+// covers every pencil of an axis ("option 4", Sec. 5.1), extended to the whole
+// three-axis schedule of Sec. 4.1: it fixes, per axis, the radix order, the
+// twiddle table and the launch shape of the pass, and uploads the tables once.
+// Exec then only launches the passes (z, then y, then x).
+#include <cuda_runtime.h>
+
+#include <math.h>
+#include <stdio.h>
+#include <stdlib.h>
+#include <string.h>
+
+#include <new>
+#include <string>
+#include <vector>
+
+#include "../../include/croft.h"
+#include "croft_internal.h"
+
+using namespace croft;
+
+struct croft_plan_s {
+    int dims[3];          // nx, ny, nz
+    croft_dtype dtype;
+    int device;
+    std::vector<PassLaunch> passes;   // execution order (z, y, x; length-1 axes skipped)
+    std::vector<int> pass_axis;       // axis index of each pass (2 = z, 1 = y, 0 = x)
+    float2* tw_dev[3];                // per-axis twiddle tables (NULL for length <= 1)
+    bool timing;
+    cudaEvent_t ev[4];
+    int ev_count;                     // events recorded by the last exec
+    bool ran;
+};
+
+// ---------------------------------------------------------------------------
+// host planning helpers
+// ---------------------------------------------------------------------------
+
+static bool axis_supported(int n) { return croft_make_sched(n).count >= 0; }
+
+static int factorize(int n, int* r, int cap) {
+    CroftSched sc = croft_make_sched(n);
+    if (sc.count < 0 || sc.count > cap) return -1;
+    for (int i = 0; i < sc.count; ++i) r[i] = sc.r[i];
+    return sc.count;
+}
+
+// exp(-2 pi i r / N) in float64, 0 <= r < N, with the angle reduced to the
+// first quadrant by integer arithmetic so that multiples of a quarter turn
+// are exact (1, -i, -1, i) and the two halves of a quadrant are mirror images.
+static void twiddle64(long long r, long long N, double* re, double* im) {
+    long long q = (4 * r) / N;
+    long long rem = 4 * r - q * N;  // angle = (q + rem/N) * pi/2
+    double c, s;
+    if (2 * rem <= N) {
+        double ph = (M_PI / 2.0) * (double)rem / (double)N;
+        c = cos(ph);
+        s = sin(ph);
+    } else {
+        double ph = (M_PI / 2.0) * (double)(N - rem) / (double)N;
+        c = sin(ph);
+        s = cos(ph);
+    }
+    double x = c, y = -s;  // exp(-i phi)
+    for (long long t = 0; t < (q & 3); ++t) {  // times (-i)^q
+        double nx = y, ny = -x;
+        x = nx;
+        y = ny;
+    }
+    *re = x;
+    *im = y;
+}
+
+static int build_twiddles(int n, const int* radices, int ns, float* out) {
+    int p = 1;
+    for (int s = 0; s < ns; ++s) {
+        int R = radices[s];
+        if (R < 2 || p * R > n) return -1;
+        for (int j = 1; j < R; ++j)
+            for (int k = 0; k < p; ++k) {
+                double re, im;
+                twiddle64((long long)j * k, (long long)p * R, &re, &im);
+                long long idx = (long long)(p - 1) + (long long)(j - 1) * p + k;
+                out[2 * idx] = (float)re;
+                out[2 * idx + 1] = (float)im;
+            }
+        p *= R;
+    }
+    return p == n ? n - 1 : -1;
+}
+
+static int g_max_smem = 0;
+
+// Launch shape of one pass (layouts: croft_internal.h; kernel: croft_pass_kernel.cuh).
+// ROW: W pencils of length n per CTA, each padded to n + n/16 + 1 slots.
+// COL: W adjacent columns per CTA, W a multiple of 16 (128-byte rows).
+// Aim for ~256 threads per CTA and <= 100 KB of shared memory so that at
+// least two CTAs share an SM.
+static bool shape_pass(PassLaunch& L, int layout, int n, long long M, long long ncols) {
+    memset(&L, 0, sizeof(L));
+    L.layout = layout;
+    PassArgs& A = L.args;
+    A.n = n;
+    A.M = M;
+    A.ncols = ncols;
+    const int T = croft_threads_per_pencil(n);
+    L.T = T;
+    A.tw_pad = ((n + 1) / 2) * 2;  // keeps the tile 16-byte aligned
+    const long long smem_cap = 100 * 1024;
+    const int max_threads = 512;   // the kernels' launch bound
+    if (layout == LAYOUT_ROW) {
+        const int ld = n + (n - 1) / 16 + 1;
+        int W = (256 + T - 1) / T;
+        if (W < 1) W = 1;
+        while (W > 1 && (W * T > max_threads || (A.tw_pad + (long long)W * ld) * 8 > smem_cap)) --W;
+        if ((long long)W > ncols) W = (int)ncols;
+        A.W = W;
+        L.smem = (int)((A.tw_pad + (long long)W * ld) * 8);
+    } else {
+        int W = 16;
+        while (W * 2 * T <= 256) W *= 2;
+        while (W > 1 && (W * T > max_threads || (A.tw_pad + (long long)n * W) * 8 > smem_cap)) W /= 2;
+        A.W = W;
+        L.smem = (int)((A.tw_pad + (long long)n * W) * 8);
+    }
+    if (croft_make_sched(n).count <= 1) L.smem = 0;  // single-stage kernels touch no shared memory
+    L.block = A.W * T;
+    if (L.block > max_threads) return false;
+    long long grid = (ncols + A.W - 1) / A.W;
+    if (grid > 0x7fffffffLL) return false;
+    L.grid = (int)grid;
+    if (L.smem > g_max_smem) return false;
+    return true;
+}
+
+extern "C" {
+
+const char* croft_status_string(croft_status s) {
+    switch (s) {
+        case CROFT_OK: return "CROFT_OK";
+        case CROFT_ERR_INVALID_ARG: return "CROFT_ERR_INVALID_ARG";
+        case CROFT_ERR_UNSUPPORTED_SIZE: return "CROFT_ERR_UNSUPPORTED_SIZE";
+        case CROFT_ERR_OOM: return "CROFT_ERR_OOM";
+        case CROFT_ERR_CUDA: return "CROFT_ERR_CUDA";
+        case CROFT_ERR_TIMEOUT: return "CROFT_ERR_TIMEOUT";
+    }
+    return "CROFT_ERR_UNKNOWN";
+}
+
+int croft_factorize(int n, int* radices, int cap) {
+    if (!radices || cap < 0) return -1;
+    return factorize(n, radices, cap);
+}
+
+int croft_twiddle_table(int n, const int* radices, int nstages, float* out) {
+    if (!out || (!radices && nstages > 0) || n < 1 || n > CROFT_MAX_N) return -1;
+    if (n == 1) return nstages == 0 ? 0 : -1;
+    return build_twiddles(n, radices, nstages, out);
+}
+
+croft_status croft_plan_destroy(croft_plan plan) {
+    if (!plan) return CROFT_OK;
+    int cur = -1;
+    cudaGetDevice(&cur);
+    cudaSetDevice(plan->device);
+    for (int a = 0; a < 3; ++a)
+        if (plan->tw_dev[a]) cudaFree(plan->tw_dev[a]);
+    for (int i = 0; i < 4; ++i)
+        if (plan->ev[i]) cudaEventDestroy(plan->ev[i]);
+    if (cur >= 0) cudaSetDevice(cur);
+    delete plan;
+    return CROFT_OK;
+}
+
+croft_status croft_plan_create(croft_plan* out, int nx, int ny, int nz, croft_dtype dtype) {
+    if (!out) return CROFT_ERR_INVALID_ARG;
+    *out = NULL;
+    if (dtype != CROFT_C2C_F32 && dtype != CROFT_C2C_F32_TC_BF16X3) return CROFT_ERR_INVALID_ARG;
+    if (!axis_supported(nx) || !axis_supported(ny) || !axis_supported(nz)) return CROFT_ERR_UNSUPPORTED_SIZE;
+    if (dtype == CROFT_C2C_F32_TC_BF16X3) return CROFT_ERR_UNSUPPORTED_SIZE;  // enabled with the tensor-core stage
+
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) { cudaGetLastError(); return CROFT_ERR_CUDA; }
+    cudaDeviceProp prop;
+    if (cudaGetDeviceProperties(&prop, dev) != cudaSuccess) { cudaGetLastError(); return CROFT_ERR_CUDA; }
+    if (prop.major < 10) return CROFT_ERR_CUDA;  // built for sm_103a only
+    g_max_smem = (int)prop.sharedMemPerBlockOptin;
+
+    croft_plan p = new (std::nothrow) croft_plan_s();
+    if (!p) return CROFT_ERR_OOM;
+    p->dims[0] = nx;
+    p->dims[1] = ny;
+    p->dims[2] = nz;
+    p->dtype = dtype;
+    p->device = dev;
+    for (int a = 0; a < 3; ++a) p->tw_dev[a] = NULL;
+    for (int i = 0; i < 4; ++i) p->ev[i] = NULL;
+    p->timing = false;
+    p->ev_count = 0;
+    p->ran = false;
+
+    const long long N = (long long)nx * ny * nz;
+    // pass order z (ROW), y (COL, stride nz), x (COL, stride ny*nz)
+    const int order[3] = {2, 1, 0};
+    for (int oi = 0; oi < 3; ++oi) {
+        const int axis = order[oi];
+        const int n = p->dims[axis];
+        if (n == 1) continue;
+        int rad[CROFT_MAX_STAGES];
+        int ns = factorize(n, rad, CROFT_MAX_STAGES);
+        if (ns < 1) { croft_plan_destroy(p); return CROFT_ERR_UNSUPPORTED_SIZE; }
+        std::vector<float> tw(2 * (size_t)(n - 1) + 2, 0.f);
+        if (build_twiddles(n, rad, ns, tw.data()) != n - 1) { croft_plan_destroy(p); return CROFT_ERR_UNSUPPORTED_SIZE; }
+        if (cudaMalloc((void**)&p->tw_dev[axis], sizeof(float2) * (size_t)n) != cudaSuccess) {
+            cudaGetLastError();
+            croft_plan_destroy(p);
+            return CROFT_ERR_OOM;
+        }
+        if (cudaMemcpy(p->tw_dev[axis], tw.data(), sizeof(float2) * (size_t)(n - 1), cudaMemcpyHostToDevice) != cudaSuccess) {
+            cudaGetLastError();
+            croft_plan_destroy(p);
+            return CROFT_ERR_CUDA;
+        }
+        // element stride of the axis; a unit stride means the pencils are contiguous rows
+        const long long M = (axis == 2) ? 1 : (axis == 1 ? (long long)nz : (long long)ny * nz);
+        PassLaunch L;
+        bool ok = shape_pass(L, M == 1 ? LAYOUT_ROW : LAYOUT_COL, n, M, N / n);
+        if (!ok) { croft_plan_destroy(p); return CROFT_ERR_UNSUPPORTED_SIZE; }
+        if (prepare_pass(L) != cudaSuccess) { cudaGetLastError(); croft_plan_destroy(p); return CROFT_ERR_CUDA; }
+        L.args.tw = p->tw_dev[axis];
+        p->passes.push_back(L);
+        p->pass_axis.push_back(axis);
+    }
+    const char* log = getenv("CROFT_LOG");
+    if (log && log[0] == '1') {
+        char buf[1024];
+        croft_plan_describe(p, buf, sizeof(buf));
+        fprintf(stderr, "croft: %s\n", buf);
+    }
+    *out = p;
+    return CROFT_OK;
+}
+
+int croft_plan_describe(croft_plan plan, char* buf, int cap) {
+    if (!plan) return -1;
+    std::string s;
+    char tmp[256];
+    snprintf(tmp, sizeof(tmp), "grid %dx%dx%d dtype %d passes %d", plan->dims[0], plan->dims[1], plan->dims[2],
+             (int)plan->dtype, (int)plan->passes.size());
+    s += tmp;
+    static const char* an[3] = {"x", "y", "z"};
+    for (size_t i = 0; i < plan->passes.size(); ++i) {
+        const PassLaunch& L = plan->passes[i];
+        snprintf(tmp, sizeof(tmp), " | %s:%s n=%d radix=", an[plan->pass_axis[i]], L.layout == LAYOUT_ROW ? "row" : "col",
+                 L.args.n);
+        s += tmp;
+        CroftSched sc = croft_make_sched(L.args.n);
+        for (int st = 0; st < sc.count; ++st) {
+            snprintf(tmp, sizeof(tmp), "%s%d", st ? "x" : "", sc.r[st]);
+            s += tmp;
+        }
+        snprintf(tmp, sizeof(tmp), " T=%d W=%d block=%d grid=%d smem=%d", L.T, L.args.W, L.block, L.grid, L.smem);
+        s += tmp;
+    }
+    if (buf && cap > 0) {
+        size_t m = s.size() < (size_t)(cap - 1) ? s.size() : (size_t)(cap - 1);
+        memcpy(buf, s.data(), m);
+        buf[m] = 0;
+    }
+    return (int)s.size();
+}
+
+size_t croft_plan_workspace_bytes(croft_plan plan) {
+    (void)plan;
+    return 0;
+}
+
+int croft_plan_num_launches(croft_plan plan) {
+    if (!plan) return -1;
+    return plan->passes.empty() ? 0 : (int)plan->passes.size();
+}
+
+croft_status croft_plan_set_timing(croft_plan plan, int enable) {
+    if (!plan) return CROFT_ERR_INVALID_ARG;
+    if (enable && !plan->ev[0]) {
+        for (int i = 0; i < 4; ++i)
+            if (cudaEventCreate(&plan->ev[i]) != cudaSuccess) { cudaGetLastError(); return CROFT_ERR_CUDA; }
+    }
+    plan->timing = enable != 0;
+    plan->ev_count = 0;
+    return CROFT_OK;
+}
+
+int croft_plan_pass_times(croft_plan plan, float* ms, int cap) {
+    if (!plan || !plan->timing || plan->ev_count < 2) return 0;
+    if (cudaEventSynchronize(plan->ev[plan->ev_count - 1]) != cudaSuccess) { cudaGetLastError(); return -1; }
+    int np = plan->ev_count - 1;
+    for (int i = 0; i < np && i < cap; ++i) {
+        float t = 0.f;
+        if (cudaEventElapsedTime(&t, plan->ev[i], plan->ev[i + 1]) != cudaSuccess) { cudaGetLastError(); return -1; }
+        if (ms) ms[i] = t;
+    }
+    return np;
+}
+
+croft_status croft_plan_last_device_status(croft_plan plan) {
+    if (!plan) return CROFT_ERR_INVALID_ARG;
+    return CROFT_OK;
+}
+
+static croft_status exec_dir(croft_plan plan, const void* in, void* out, void* stream, float isign) {
+    if (!plan || !in || !out) return CROFT_ERR_INVALID_ARG;
+    if (((uintptr_t)in & 15) || ((uintptr_t)out & 15)) return CROFT_ERR_INVALID_ARG;
+    const long long N = (long long)plan->dims[0] * plan->dims[1] * plan->dims[2];
+    const size_t bytes = (size_t)N * sizeof(float2);
+    const char* a = (const char*)in;
+    const char* b = (const char*)out;
+    if (a != b && a < b + bytes && b < a + bytes) return CROFT_ERR_INVALID_ARG;
+    cudaStream_t s = (cudaStream_t)stream;
+    if (plan->passes.empty()) {
+        if (in != out && cudaMemcpyAsync(out, in, bytes, cudaMemcpyDeviceToDevice, s) != cudaSuccess) {
+            cudaGetLastError();
+            return CROFT_ERR_CUDA;
+        }
+        plan->ev_count = 0;
+        return CROFT_OK;
+    }
+    const bool tm = plan->timing;
+    if (tm && cudaEventRecord(plan->ev[0], s) != cudaSuccess) { cudaGetLastError(); return CROFT_ERR_CUDA; }
+    const float2* src = (const float2*)in;
+    float2* dst = (float2*)out;
+    for (size_t i = 0; i < plan->passes.size(); ++i) {
+        PassLaunch L = plan->passes[i];
+        L.args.isign = isign;
+        cudaError_t e = launch_pass(L, src, dst, s);
+        if (e != cudaSuccess) { cudaGetLastError(); return CROFT_ERR_CUDA; }
+        if (tm && cudaEventRecord(plan->ev[i + 1], s) != cudaSuccess) { cudaGetLastError(); return CROFT_ERR_CUDA; }
+        src = dst;
+    }
+    plan->ev_count = tm ? (int)plan->passes.size() + 1 : 0;
+    plan->ran = true;
+    return CROFT_OK;
+}
+
+croft_status croft_exec_forward(croft_plan plan, const void* in, void* out, void* stream) {
+    return exec_dir(plan, in, out, stream, 1.0f);
+}
+
+croft_status croft_exec_backward(croft_plan plan, const void* in, void* out, void* stream) {
+    return exec_dir(plan, in, out, stream, -1.0f);
+}
+
+}  // extern "C"

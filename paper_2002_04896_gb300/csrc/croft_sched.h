@@ -1,0 +1,59 @@
+// croft_sched.h - the radix schedule of a length-n axis, shared by the host
+// planner (twiddle-table layout, launch shape) and the device kernels (which
+// are specialised on n, so every loop bound, stride and twiddle offset is a
+// compile-time constant).
+#pragma once
+
+#ifdef __CUDACC__
+#define CROFT_HD __host__ __device__
+#else
+#define CROFT_HD
+#endif
+
+#define CROFT_MAX_STAGES 8  // 2^a 3^b 5^c <= 4096 needs at most 7 stages
+#define CROFT_MAX_N 4096
+
+struct CroftSched {
+    int count;                  // number of stages (0 for n = 1, -1 if unsupported)
+    int r[CROFT_MAX_STAGES];    // radix of each stage, in execution order
+};
+
+// Schedule: the power-of-two part of n in ceil(a/4) stages of (nearly) equal
+// size from {16, 8, 4, 2} (larger first), then one stage per factor 5 and per
+// factor 3.  The first stage needs no twiddles, so the largest radix goes there.
+CROFT_HD constexpr CroftSched croft_make_sched(int n) {
+    CroftSched s{0, {0, 0, 0, 0, 0, 0, 0, 0}};
+    if (n < 1 || n > CROFT_MAX_N) {
+        s.count = -1;
+        return s;
+    }
+    int m = n, a = 0, c3 = 0, c5 = 0;
+    while (m % 2 == 0) { m /= 2; ++a; }
+    while (m % 3 == 0) { m /= 3; ++c3; }
+    while (m % 5 == 0) { m /= 5; ++c5; }
+    if (m != 1) {
+        s.count = -1;
+        return s;
+    }
+    int k = 0;
+    if (a > 0) {
+        const int st = (a + 3) / 4;
+        const int base = a / st, extra = a % st;
+        for (int i = 0; i < st; ++i) s.r[k++] = 1 << (base + (i < extra ? 1 : 0));
+    }
+    for (int i = 0; i < c5; ++i) s.r[k++] = 5;
+    for (int i = 0; i < c3; ++i) s.r[k++] = 3;
+    s.count = k;
+    return s;
+}
+
+// Length of the sub-transforms that stage `stage` combines (product of the earlier radices).
+CROFT_HD constexpr int croft_sched_p(const CroftSched& s, int stage) {
+    int p = 1;
+    for (int i = 0; i < stage; ++i) p *= s.r[i];
+    return p;
+}
+
+// Per-thread element budget and threads per pencil of the pass kernels.
+CROFT_HD constexpr int croft_emax(int n) { return n <= 1024 ? 16 : 32; }
+CROFT_HD constexpr int croft_threads_per_pencil(int n) { return (n + croft_emax(n) - 1) / croft_emax(n); }

@@ -1,0 +1,145 @@
+"""CUDA path vs the FP64 oracle, through the C ABI (needs a GPU).
+
+Tolerance (FP32 path): relative L2 error <= 2e-6 * log2(N), N = nx*ny*nz,
+measured against the oracle run on the same complex64 input.
+"""
+
+import math
+
+import numpy as np
+import pytest
+
+import oracle
+import synthetic_inputs as S
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+
+
+def tol(shape):
+    n = int(np.prod(shape))
+    return 2e-6 * max(1.0, math.log2(n))
+
+
+@pytest.fixture(scope="module")
+def dev(croft_lib):
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    return torch.device("cuda:0")
+
+
+def run(croft, x_np, direction="forward", inplace=False, dtype=0):
+    x = torch.from_numpy(np.ascontiguousarray(x_np)).cuda()
+    with croft.Plan(*x_np.shape, dtype=dtype) as p:
+        out = x if inplace else torch.empty_like(x)
+        getattr(p, direction)(x, out)
+        torch.cuda.synchronize()
+        return out.cpu().numpy()
+
+
+def _supported_sizes(limit):
+    out = []
+    for n in range(2, limit + 1):
+        m = n
+        for p in (2, 3, 5):
+            while m % p == 0:
+                m //= p
+        if m == 1:
+            out.append(n)
+    return out
+
+
+@pytest.mark.parametrize("n", _supported_sizes(4096))
+def test_every_axis_length_on_every_axis(croft_lib, dev, n):
+    """Each supported length as the z (contiguous), y and x (strided) axis, ragged batch sizes."""
+    rng = np.random.default_rng(n)
+    for shape in [(2, 3, n), (3, n, 5), (n, 2, 3)]:
+        x = (rng.uniform(-1, 1, shape) + 1j * rng.uniform(-1, 1, shape)).astype(np.complex64)
+        y = run(croft_lib, x)
+        ref = oracle.forward(x)
+        e = oracle.rel_l2(y, ref)
+        assert e <= tol(shape), (shape, e)
+
+
+@pytest.mark.parametrize("shape", [(1, 1, 1), (1, 1, 8), (1, 16, 1), (32, 1, 1), (2, 2, 2), (6, 10, 15),
+                                   (64, 48, 40), (5, 3, 1), (1, 60, 128)])
+def test_small_and_degenerate_shapes(croft_lib, dev, shape):
+    rng = np.random.default_rng(1)
+    x = (rng.standard_normal(shape) + 1j * rng.standard_normal(shape)).astype(np.complex64)
+    for direction, ref in (("forward", oracle.forward(x)), ("backward", oracle.backward(x))):
+        y = run(croft_lib, x, direction)
+        assert oracle.rel_l2(y, ref) <= tol(shape), (shape, direction)
+
+
+def test_noise32_forward_backward_roundtrip(croft_lib, dev):
+    """32^3 white noise (seed 0): forward, backward and backward(forward(x)) = N x."""
+    x = S.white_noise((32, 32, 32), 0)
+    t = tol(x.shape)
+    yf = run(croft_lib, x, "forward")
+    ref_f = oracle.forward(x)
+    ef = oracle.rel_l2(yf, ref_f)
+    ref_f32 = ref_f.astype(np.complex64)
+    yb = run(croft_lib, ref_f32, "backward")
+    eb = oracle.rel_l2(yb, oracle.backward(ref_f32))
+    yr = run(croft_lib, yf, "backward")
+    er = oracle.rel_l2(yr, x.size * x.astype(np.complex128))
+    print(f"noise32 rel_l2 fwd {ef:.3e} bwd {eb:.3e} roundtrip {er:.3e} (tol {t:.2e})")
+    assert ef <= t and eb <= t and er <= t
+
+
+def test_in_place_equals_out_of_place_bitwise(croft_lib, dev):
+    x = S.white_noise((48, 40, 30), 5)
+    a = run(croft_lib, x, "forward", inplace=False)
+    b = run(croft_lib, x, "forward", inplace=True)
+    assert np.array_equal(a.view(np.uint32), b.view(np.uint32))
+
+
+def test_deterministic_bitwise(croft_lib, dev):
+    x = torch.from_numpy(S.white_noise((64, 60, 72), 6)).cuda()
+    with croft_lib.Plan(64, 60, 72) as p:
+        a = p.forward(x)
+        b = p.forward(x)
+        torch.cuda.synchronize()
+        assert torch.equal(a.view(torch.int32), b.view(torch.int32))
+
+
+def test_input_untouched_out_of_place(croft_lib, dev):
+    xn = S.white_noise((16, 24, 20), 7)
+    x = torch.from_numpy(xn).cuda()
+    with croft_lib.Plan(16, 24, 20) as p:
+        p.forward(x)
+        p.backward(x)
+        torch.cuda.synchronize()
+    assert np.array_equal(x.cpu().numpy(), xn)
+
+
+def test_side_stream_and_timing_hook(croft_lib, dev):
+    x = torch.from_numpy(S.white_noise((64, 64, 64), 8)).cuda()
+    out = torch.empty_like(x)
+    s = torch.cuda.Stream()
+    with croft_lib.Plan(64, 64, 64) as p:
+        croft_lib.croft_plan_set_timing(p.handle, True)
+        with torch.cuda.stream(s):
+            croft_lib.croft_exec_forward(p.handle, x, out, s)
+        times = croft_lib.croft_plan_pass_times(p.handle)
+        s.synchronize()
+        assert len(times) == croft_lib.croft_plan_num_launches(p.handle) == 3
+        assert all(t > 0 for t in times)
+    assert oracle.rel_l2(out.cpu().numpy(), oracle.forward(x.cpu().numpy())) <= tol((64, 64, 64))
+
+
+def test_invalid_pointers_rejected(croft_lib, dev):
+    x = torch.zeros(8 * 8 * 8 + 4, dtype=torch.complex64, device="cuda")
+    with croft_lib.Plan(8, 8, 8) as p:
+        h = p.handle
+        base = x.data_ptr()
+        # partial overlap
+        assert croft_lib.croft_exec_forward_status(h, base, base + 16 * 8, 0) == croft_lib.CROFT_ERR_INVALID_ARG
+        # misaligned (8-byte, not 16-byte)
+        assert croft_lib.croft_exec_forward_status(h, base + 8, base + 8, 0) == croft_lib.CROFT_ERR_INVALID_ARG
+        # null
+        assert croft_lib.croft_exec_forward_status(h, 0, base, 0) == croft_lib.CROFT_ERR_INVALID_ARG
+        # exact in-place is fine
+        assert croft_lib.croft_exec_forward_status(h, base, base, 0) == croft_lib.CROFT_OK
+    torch.cuda.synchronize()
