@@ -83,7 +83,7 @@ def ncu_traffic(kernel_key: str):
 
 
 class ClockSampler:
-    """nvidia-smi clocks / throttle reasons sampled every 200 ms while active."""
+    """nvidia-smi clocks / throttle reasons sampled every 100 ms while active."""
 
     FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
               "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
@@ -99,7 +99,7 @@ class ClockSampler:
         try:
             self.proc = subprocess.Popen(
                 ["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
-                 "-lms", "200"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+                 "-lms", "100"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
         except Exception:  # noqa: BLE001
             self.proc = None
             return
@@ -238,16 +238,19 @@ def run_croft(args):
     y = torch.empty_like(x)
     z = torch.empty_like(x)
     l2 = torch.cuda.get_device_properties(dev).L2_cache_size
-    flush = torch.empty(max(2 * l2, 256 << 20) // 4, dtype=torch.float32, device=dev)
+    flush = torch.empty(max(2 * l2, 1 << 30) // 4, dtype=torch.float32, device=dev)
 
     plan = croft.Plan(*shape)
     croft.croft_plan_set_timing(plan.handle, True)
     launches_per_step = 2 * croft.croft_plan_num_launches(plan.handle)
     sh = stream.cuda_stream
 
+    gap_fills = [1]
+
     def step(record):
         with torch.cuda.stream(stream):
-            flush.fill_(1.0)
+            for _ in range(gap_fills[0]):
+                flush.fill_(1.0)
             e = [torch.cuda.Event(enable_timing=True) for _ in range(4)]
             e[0].record(stream)
             croft.croft_exec_forward(plan.handle, x, y, sh)
@@ -264,6 +267,19 @@ def run_croft(args):
 
     for _ in range(args.warmup):
         step(None)
+    # Untimed L2-flush writes between timed steps keep the GPU busy so that the
+    # timed region spans >= ~2 s of wall time: long enough for the clock samples
+    # to describe it, without idle gaps that would let the clocks drop.
+    with torch.cuda.stream(stream):
+        a = torch.cuda.Event(enable_timing=True)
+        b = torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        for _ in range(10):
+            flush.fill_(1.0)
+        b.record(stream)
+    stream.synchronize()
+    t_fill = a.elapsed_time(b) / 10 * 1e-3
+    gap_fills[0] = max(1, int(math.ceil(args.clock_window_s / max(1, args.steps) / t_fill)))
     if world > 1:
         torch.distributed.barrier()
     torch.cuda.synchronize()
@@ -343,7 +359,7 @@ def run_croft(args):
             "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f32", "data": "synthetic",
             "config": {"workload": WORKLOAD, "grid": list(shape), "direction": "forward+backward",
-                       "l2": "flushed before every step (write of a 2x L2 buffer, outside the timed events)",
+                       "l2": "flushed before every step (writes of a 1 GiB buffer, > 2x L2, outside the timed events)",
                        "parallelism": f"replicas x{world}" if world > 1 else "single GPU",
                        "passes_per_direction": npass},
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
@@ -371,6 +387,9 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="croft", choices=["croft", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--clock-window-s", type=float, default=2.0,
+                    help="minimum wall time of the timed region, padded with untimed L2-flush writes "
+                         "between steps (0 under a profiler)")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
