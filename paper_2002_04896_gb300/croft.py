@@ -88,9 +88,23 @@ def _stream_ptr(stream) -> int:
     return int(stream.cuda_stream)
 
 
-def _ptr(x) -> int:
+def _ptr(x, numel=None) -> int:
+    """Device address of a raw pointer (int) or of a C-contiguous complex64 CUDA tensor."""
+    if x is None:
+        return 0
     if isinstance(x, int):
         return x
+    import torch
+    if not isinstance(x, torch.Tensor):
+        raise TypeError("expected a torch CUDA tensor or an integer device address")
+    if not x.is_cuda:
+        raise ValueError("croft: tensors must live on a CUDA device")
+    if x.dtype != torch.complex64:
+        raise ValueError(f"croft: expected complex64, got {x.dtype}")
+    if not x.is_contiguous():
+        raise ValueError("croft: tensors must be C-contiguous in (nx, ny, nz) order")
+    if numel is not None and x.numel() != numel:
+        raise ValueError(f"croft: tensor has {x.numel()} elements, plan expects {numel}")
     return int(x.data_ptr())
 
 
@@ -189,18 +203,21 @@ class Plan:
         self.dtype = dtype
         self.handle = croft_plan_create(nx, ny, nz, dtype)
 
-    def forward(self, inp, out=None, stream=None):
+    def _out(self, inp, out):
         if out is None:
             import torch
-            out = torch.empty_like(inp)
-        croft_exec_forward(self.handle, inp, out, stream)
+            out = torch.empty(self.shape, dtype=torch.complex64, device=inp.device)
+        n = self.shape[0] * self.shape[1] * self.shape[2]
+        return _ptr(inp, n), _ptr(out, n), out
+
+    def forward(self, inp, out=None, stream=None):
+        pi, po, out = self._out(inp, out)
+        croft_exec_forward(self.handle, pi, po, stream)
         return out
 
     def backward(self, inp, out=None, stream=None):
-        if out is None:
-            import torch
-            out = torch.empty_like(inp)
-        croft_exec_backward(self.handle, inp, out, stream)
+        pi, po, out = self._out(inp, out)
+        croft_exec_backward(self.handle, pi, po, stream)
         return out
 
     def describe(self) -> str:

@@ -32,7 +32,7 @@ def _check_grid(croft, x):
         yf_h = yf.cpu().numpy()
         ref_f = oracle.forward(x)
         ef = oracle.rel_l2(yf_h, ref_f)
-        ref_f32 = ref_f.astype(np.complex64)
+        ref_f32 = np.ascontiguousarray(ref_f, dtype=np.complex64)
         yb = p.backward(torch.from_numpy(ref_f32).cuda())
         torch.cuda.synchronize()
         eb = oracle.rel_l2(yb.cpu().numpy(), oracle.backward(ref_f32))

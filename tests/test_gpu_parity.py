@@ -79,7 +79,7 @@ def test_noise32_forward_backward_roundtrip(croft_lib, dev):
     yf = run(croft_lib, x, "forward")
     ref_f = oracle.forward(x)
     ef = oracle.rel_l2(yf, ref_f)
-    ref_f32 = ref_f.astype(np.complex64)
+    ref_f32 = np.ascontiguousarray(ref_f, dtype=np.complex64)
     yb = run(croft_lib, ref_f32, "backward")
     eb = oracle.rel_l2(yb, oracle.backward(ref_f32))
     yr = run(croft_lib, yf, "backward")
@@ -143,3 +143,14 @@ def test_invalid_pointers_rejected(croft_lib, dev):
         # exact in-place is fine
         assert croft_lib.croft_exec_forward_status(h, base, base, 0) == croft_lib.CROFT_OK
     torch.cuda.synchronize()
+
+
+def test_binding_rejects_non_contiguous_and_wrong_dtype(croft_lib, dev):
+    x = torch.zeros((8, 6, 4), dtype=torch.complex64, device="cuda")
+    with croft_lib.Plan(8, 6, 4) as p:
+        with pytest.raises(ValueError):
+            p.forward(x.permute(2, 1, 0).contiguous().permute(2, 1, 0))  # right shape, permuted strides
+        with pytest.raises(ValueError):
+            p.forward(x.to(torch.complex128))
+        with pytest.raises(ValueError):
+            p.forward(torch.zeros((8, 6, 5), dtype=torch.complex64, device="cuda"))
