@@ -79,6 +79,30 @@ const char* croft_status_string(croft_status s);
 croft_status croft_plan_create(croft_plan* out, int nx, int ny, int nz, croft_dtype dtype);
 
 /*
+ * Pass schedules.
+ *   CROFT_SCHEDULE_THREE_PASS : one pass per axis (z, y, x): the paper's three
+ *       1D-FFT steps (Sec. 4.1, steps 1, 5, 9) with each rearrangement fused
+ *       into the next pass; the grid crosses HBM three times per transform.
+ *   CROFT_SCHEDULE_PLANE_FUSED : steps 1-5 as one pass (the 2D FFT of every
+ *       yz-plane, one plane per thread-block cluster, the column all-to-all
+ *       done through distributed shared memory), then the x pass; the grid
+ *       crosses HBM twice.  Available for the plane shapes the library
+ *       instantiates (ny x nz in {32x32, 64x64, 128x128, 256x256, 384x384,
+ *       480x480, 512x512, 360x320}); other shapes give CROFT_ERR_UNSUPPORTED_SIZE.
+ *   CROFT_SCHEDULE_AUTO : PLANE_FUSED when available, else THREE_PASS.
+ */
+typedef enum {
+    CROFT_SCHEDULE_AUTO = 0,
+    CROFT_SCHEDULE_THREE_PASS = 1,
+    CROFT_SCHEDULE_PLANE_FUSED = 2
+} croft_schedule;
+
+/* croft_plan_create with an explicit schedule (same arguments and errors;
+ * CROFT_ERR_INVALID_ARG for an unknown schedule). */
+croft_status croft_plan_create_schedule(croft_plan* out, int nx, int ny, int nz, croft_dtype dtype,
+                                        croft_schedule schedule);
+
+/*
  * croft_exec_forward - Eq. (1), unnormalised, out = F(in).
  * croft_exec_backward - Eq. (2) with exponent +, WITHOUT the 1/N factor.
  *

@@ -20,6 +20,10 @@ _lib = ctypes.CDLL(_LIB_PATH)
 CROFT_C2C_F32 = 0
 CROFT_C2C_F32_TC_BF16X3 = 1
 
+CROFT_SCHEDULE_AUTO = 0
+CROFT_SCHEDULE_THREE_PASS = 1
+CROFT_SCHEDULE_PLANE_FUSED = 2
+
 CROFT_OK = 0
 CROFT_ERR_INVALID_ARG = 1
 CROFT_ERR_UNSUPPORTED_SIZE = 2
@@ -40,6 +44,7 @@ def _sig(name, res, args):
 
 _status_string = _sig("croft_status_string", ctypes.c_char_p, [_I])
 _plan_create = _sig("croft_plan_create", _I, [ctypes.POINTER(_P), _I, _I, _I, _I])
+_plan_create_schedule = _sig("croft_plan_create_schedule", _I, [ctypes.POINTER(_P), _I, _I, _I, _I, _I])
 _exec_forward = _sig("croft_exec_forward", _I, [_P, _P, _P, _P])
 _exec_backward = _sig("croft_exec_backward", _I, [_P, _P, _P, _P])
 _workspace_bytes = _sig("croft_plan_workspace_bytes", ctypes.c_size_t, [_P])
@@ -54,7 +59,7 @@ _twiddle_table = _sig("croft_twiddle_table", _I, [_I, ctypes.POINTER(_I), _I, ct
 
 LIBRARY_PATH = _LIB_PATH
 EXPORTED = [
-    "croft_status_string", "croft_plan_create", "croft_exec_forward", "croft_exec_backward",
+    "croft_status_string", "croft_plan_create", "croft_plan_create_schedule", "croft_exec_forward", "croft_exec_backward",
     "croft_plan_workspace_bytes", "croft_plan_num_launches", "croft_plan_describe", "croft_plan_set_timing",
     "croft_plan_pass_times", "croft_plan_last_device_status", "croft_plan_destroy", "croft_factorize",
     "croft_twiddle_table",
@@ -112,9 +117,12 @@ def _ptr(x, numel=None) -> int:
 # raw entry points (status codes returned, not raised)
 # ---------------------------------------------------------------------------
 
-def croft_plan_create_status(nx: int, ny: int, nz: int, dtype: int = CROFT_C2C_F32):
+def croft_plan_create_status(nx: int, ny: int, nz: int, dtype: int = CROFT_C2C_F32, schedule=None):
     h = _P()
-    st = _plan_create(ctypes.byref(h), int(nx), int(ny), int(nz), int(dtype))
+    if schedule is None:
+        st = _plan_create(ctypes.byref(h), int(nx), int(ny), int(nz), int(dtype))
+    else:
+        st = _plan_create_schedule(ctypes.byref(h), int(nx), int(ny), int(nz), int(dtype), int(schedule))
     return st, h.value
 
 
@@ -133,6 +141,12 @@ def croft_exec_backward_status(plan: int, inp, out, stream=None) -> int:
 def croft_plan_create(nx: int, ny: int, nz: int, dtype: int = CROFT_C2C_F32) -> int:
     st, h = croft_plan_create_status(nx, ny, nz, dtype)
     _check(st, f"croft_plan_create({nx},{ny},{nz},{dtype})")
+    return h
+
+
+def croft_plan_create_schedule(nx: int, ny: int, nz: int, dtype: int, schedule: int) -> int:
+    st, h = croft_plan_create_status(nx, ny, nz, dtype, schedule)
+    _check(st, f"croft_plan_create_schedule({nx},{ny},{nz},{dtype},{schedule})")
     return h
 
 
@@ -198,10 +212,14 @@ def croft_twiddle_table(n: int, radices):
 class Plan:
     """RAII helper around a croft plan (torch tensors in, torch tensors out)."""
 
-    def __init__(self, nx: int, ny: int, nz: int, dtype: int = CROFT_C2C_F32):
+    def __init__(self, nx: int, ny: int, nz: int, dtype: int = CROFT_C2C_F32, schedule=None):
         self.shape = (int(nx), int(ny), int(nz))
         self.dtype = dtype
-        self.handle = croft_plan_create(nx, ny, nz, dtype)
+        self.handle = None
+        if schedule is None:
+            self.handle = croft_plan_create(nx, ny, nz, dtype)
+        else:
+            self.handle = croft_plan_create_schedule(nx, ny, nz, dtype, schedule)
 
     def _out(self, inp, out):
         if out is None:

@@ -1,0 +1,159 @@
+// croft_fft_core.cuh - one Stockham stage of a length-N FFT, with pluggable operand access.
+//
+// Stage S of the length-N schedule (radix R = sched.r[S], sub-transform length
+// P = product of the earlier radices) on one pencil: butterfly b in
+// [0, N/R), k = b mod P, reads x[b + j*N/R] (j = 0..R-1), multiplies input j
+// by w_{PR}^{jk} (table entry P-1 + (j-1)*P + k), applies the radix-R DFT and
+// writes output j to y[(b-k)*R + k + j*P].  After the last stage the pencil is
+// in natural order (Stockham auto-sort).
+//
+// Where x and y live is up to the caller: `Src::load(a)` / `Dst::store(a, v)`
+// address element a of this thread's pencil in HBM, in this CTA's shared
+// memory, or in another CTA's shared memory of the same cluster.  `Mid` is the
+// barrier between the reads and the writes of the stage (needed when the
+// writes overwrite data other threads still have to read).
+#pragma once
+#include <cooperative_groups.h>
+
+#include "croft_butterflies.cuh"
+#include "croft_sched.h"
+
+namespace croft {
+
+// ---------------------------------------------------------------------------
+// operand accessors
+// ---------------------------------------------------------------------------
+
+// Pencil in HBM with element stride `stride`; conj() on the way in/out when isign = -1.
+struct GlobalIn {
+    const float2* p;
+    long long stride;
+    float isign;
+    __device__ __forceinline__ float2 load(int a) const {
+        float2 t = p[(long long)a * stride];
+        t.y *= isign;
+        return t;
+    }
+};
+struct GlobalInUnit {  // unit stride (contiguous pencil)
+    const float2* p;
+    float isign;
+    __device__ __forceinline__ float2 load(int a) const {
+        float2 t = p[a];
+        t.y *= isign;
+        return t;
+    }
+};
+struct GlobalOut {
+    float2* p;
+    long long stride;
+    float isign;
+    __device__ __forceinline__ void store(int a, float2 v) const {
+        v.y *= isign;
+        p[(long long)a * stride] = v;
+    }
+};
+struct GlobalOutUnit {
+    float2* p;
+    float isign;
+    __device__ __forceinline__ void store(int a, float2 v) const {
+        v.y *= isign;
+        p[a] = v;
+    }
+};
+
+// Row-major pencil in shared memory, one pad slot per 16 elements (conflict-free
+// for the stride-R writes of the early stages).
+__host__ __device__ constexpr int row_ld(int n) { return n + (n - 1) / 16 + 1; }
+struct SmemRow {
+    float2* s;  // start of this pencil
+    __device__ __forceinline__ float2 load(int a) const { return s[a + (a >> 4)]; }
+    __device__ __forceinline__ void store(int a, float2 v) const { s[a + (a >> 4)] = v; }
+};
+// Column c of a [N][W] tile (W pencils side by side).
+struct SmemCol {
+    float2* s;  // tile + c
+    int W;
+    __device__ __forceinline__ float2 load(int a) const { return s[a * W]; }
+    __device__ __forceinline__ void store(int a, float2 v) const { s[a * W] = v; }
+};
+
+// ---------------------------------------------------------------------------
+// barriers
+// ---------------------------------------------------------------------------
+struct NoBarrier {
+    __device__ __forceinline__ void operator()() const {}
+};
+struct CtaBarrier {
+    __device__ __forceinline__ void operator()() const { __syncthreads(); }
+};
+
+// ---------------------------------------------------------------------------
+// the stage
+// ---------------------------------------------------------------------------
+template <int N, int S, int T, class Src, class Mid, class Dst>
+__device__ __forceinline__ void fft_stage(const Src& src, const Mid& mid, const Dst& dst, const float2* stw, int lane,
+                                          bool ok) {
+    constexpr CroftSched sc = croft_make_sched(N);
+    constexpr int R = sc.r[S];
+    constexpr int P = croft_sched_p(sc, S);
+    constexpr int NB = N / R;
+    constexpr int QM = (NB + T - 1) / T;
+    float2 v[QM][R];
+#pragma unroll
+    for (int q = 0; q < QM; ++q) {
+        const int b = lane + q * T;
+        if (ok && (NB % T == 0 || b < NB)) {
+#pragma unroll
+            for (int j = 0; j < R; ++j) v[q][j] = src.load(b + j * NB);
+        }
+    }
+    mid();
+#pragma unroll
+    for (int q = 0; q < QM; ++q) {
+        const int b = lane + q * T;
+        if (ok && (NB % T == 0 || b < NB)) {
+            const int k = (P == 1) ? 0 : b % P;
+            if (P > 1) {
+                const float2* w = stw + (P - 1) + k;
+#pragma unroll
+                for (int j = 1; j < R; ++j) v[q][j] = cmul(v[q][j], w[(j - 1) * P]);
+            }
+            dft<R>(v[q]);
+            const int o = (b - k) * R + k;
+#pragma unroll
+            for (int j = 0; j < R; ++j) dst.store(o + j * P, v[q][j]);
+        }
+    }
+}
+
+// Stages [S, E) of a length-N FFT entirely in shared memory (in place), each
+// followed by a CTA barrier.  `Sm` is SmemRow or SmemCol.
+template <int N, int S, int E, int T, class Sm>
+__device__ __forceinline__ void smem_stages(const Sm& sm, const float2* stw, int lane, bool ok) {
+    if constexpr (S < E) {
+        fft_stage<N, S, T>(sm, CtaBarrier{}, sm, stw, lane, ok);
+        __syncthreads();
+        smem_stages<N, S + 1, E, T>(sm, stw, lane, ok);
+    }
+}
+
+// A full length-N FFT of one pencil per thread group: first stage src -> work
+// (shared memory), inner stages in `work`, last stage work -> dst.  With a
+// single-stage schedule src -> dst directly.  `work` must not alias src/dst.
+// Ends without a trailing barrier when dst is not shared memory.
+template <int N, int T, class Src, class Sm, class Dst>
+__device__ __forceinline__ void fft_pencil(const Src& src, const Sm& work, const Dst& dst, const float2* stw,
+                                           int lane, bool ok) {
+    constexpr CroftSched sc = croft_make_sched(N);
+    if constexpr (sc.count == 1) {
+        fft_stage<N, 0, T>(src, NoBarrier{}, dst, stw, lane, ok);
+    } else {
+        fft_stage<N, 0, T>(src, NoBarrier{}, work, stw, lane, ok);
+        __syncthreads();
+        smem_stages<N, 1, sc.count - 1, T>(work, stw, lane, ok);
+        fft_stage<N, sc.count - 1, T>(work, NoBarrier{}, dst, stw, lane, ok);
+    }
+}
+
+}  // namespace croft

@@ -25,8 +25,28 @@ struct PassArgs {
     float isign;        // +1 forward, -1 backward (conj-in / conj-out)
 };
 
+// Fused z+y pass: 2D FFT of every yz-plane (one plane per cluster of C CTAs).
+struct PlaneArgs {
+    const float2* tw_z;  // twiddle table of the z axis (nz-1 entries)
+    const float2* tw_y;  // twiddle table of the y axis (ny-1 entries)
+    float isign;
+};
+
+typedef void (*pass_fn)(const float2*, float2*, const PassArgs);
+typedef void (*plane_fn)(const float2*, float2*, const PlaneArgs);
+
+struct PlaneKernel {
+    plane_fn fn;
+    int ny, nz, cluster, threads, smem;
+};
+
+enum PassKind { PASS_AXIS = 0, PASS_PLANE = 1 };
+
 struct PassLaunch {
-    PassArgs args;
+    int kind;           // PASS_AXIS or PASS_PLANE
+    PassArgs args;      // PASS_AXIS
+    PlaneArgs pargs;    // PASS_PLANE
+    PlaneKernel pk;     // PASS_PLANE
     int layout;
     int T;              // threads per pencil (fixed by the kernel: croft_threads_per_pencil)
     int grid;
@@ -34,7 +54,8 @@ struct PassLaunch {
     int smem;           // dynamic shared memory bytes
 };
 
-typedef void (*pass_fn)(const float2*, float2*, const PassArgs);
+// croft_planes.cu
+const PlaneKernel* find_plane_kernel(int ny, int nz);  // NULL if no fused kernel for this plane
 
 // croft_kernels.cu, one per size group
 pass_fn lookup_pass_kernel_group_0(int layout, int n);
@@ -44,7 +65,8 @@ pass_fn lookup_pass_kernel_group_3(int layout, int n);
 
 // croft_passes.cu
 pass_fn pass_kernel_for(int layout, int n);
-cudaError_t prepare_pass(const PassLaunch& L);  // once per plan: opt in to > 48 KB shared memory
+cudaError_t prepare_pass(const PassLaunch& L);  // once per plan: shared-memory / cluster opt-ins, occupancy check
 cudaError_t launch_pass(const PassLaunch& L, const float2* in, float2* out, cudaStream_t s);
+int active_clusters(const PassLaunch& L);  // co-resident clusters of a plane pass (0 for axis passes)
 
 }  // namespace croft

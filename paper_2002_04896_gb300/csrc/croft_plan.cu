@@ -174,10 +174,54 @@ croft_status croft_plan_destroy(croft_plan plan) {
     return CROFT_OK;
 }
 
-croft_status croft_plan_create(croft_plan* out, int nx, int ny, int nz, croft_dtype dtype) {
+static croft_status fail(croft_plan p, croft_status st) {
+    cudaGetLastError();
+    croft_plan_destroy(p);
+    return st;
+}
+
+// Axis pass (z: ROW; y, x: COL) of the three-pass schedule, or the x pass of the fused one.
+static croft_status add_axis_pass(croft_plan p, int axis) {
+    const int nx = p->dims[0], ny = p->dims[1], nz = p->dims[2];
+    const long long N = (long long)nx * ny * nz;
+    const int n = p->dims[axis];
+    // element stride of the axis; a unit stride means the pencils are contiguous rows
+    const long long M = (axis == 2) ? 1 : (axis == 1 ? (long long)nz : (long long)ny * nz);
+    PassLaunch L;
+    if (!shape_pass(L, M == 1 ? LAYOUT_ROW : LAYOUT_COL, n, M, N / n)) return CROFT_ERR_UNSUPPORTED_SIZE;
+    L.kind = PASS_AXIS;
+    L.args.tw = p->tw_dev[axis];
+    if (prepare_pass(L) != cudaSuccess) return CROFT_ERR_CUDA;
+    p->passes.push_back(L);
+    p->pass_axis.push_back(axis);
+    return CROFT_OK;
+}
+
+// Fused z+y pass over every yz-plane (croft_plane_kernel.cuh).
+static croft_status add_plane_pass(croft_plan p, const PlaneKernel* pk) {
+    PassLaunch L;
+    memset(&L, 0, sizeof(L));
+    L.kind = PASS_PLANE;
+    L.pk = *pk;
+    L.pargs.tw_z = p->tw_dev[2];
+    L.pargs.tw_y = p->tw_dev[1];
+    L.grid = p->dims[0] * pk->cluster;
+    L.block = pk->threads;
+    L.smem = pk->smem;
+    L.args.n = pk->ny * pk->nz;
+    if (L.smem > g_max_smem) return CROFT_ERR_UNSUPPORTED_SIZE;
+    if (prepare_pass(L) != cudaSuccess) return CROFT_ERR_CUDA;
+    p->passes.push_back(L);
+    p->pass_axis.push_back(3);
+    return CROFT_OK;
+}
+
+static croft_status create_impl(croft_plan* out, int nx, int ny, int nz, croft_dtype dtype, croft_schedule sched) {
     if (!out) return CROFT_ERR_INVALID_ARG;
     *out = NULL;
     if (dtype != CROFT_C2C_F32 && dtype != CROFT_C2C_F32_TC_BF16X3) return CROFT_ERR_INVALID_ARG;
+    if (sched != CROFT_SCHEDULE_AUTO && sched != CROFT_SCHEDULE_THREE_PASS && sched != CROFT_SCHEDULE_PLANE_FUSED)
+        return CROFT_ERR_INVALID_ARG;
     if (!axis_supported(nx) || !axis_supported(ny) || !axis_supported(nz)) return CROFT_ERR_UNSUPPORTED_SIZE;
     if (dtype == CROFT_C2C_F32_TC_BF16X3) return CROFT_ERR_UNSUPPORTED_SIZE;  // enabled with the tensor-core stage
 
@@ -201,46 +245,62 @@ croft_status croft_plan_create(croft_plan* out, int nx, int ny, int nz, croft_dt
     p->ev_count = 0;
     p->ran = false;
 
-    const long long N = (long long)nx * ny * nz;
-    // pass order z (ROW), y (COL, stride nz), x (COL, stride ny*nz)
-    const int order[3] = {2, 1, 0};
-    for (int oi = 0; oi < 3; ++oi) {
-        const int axis = order[oi];
+    // twiddle tables, one per axis of length > 1
+    for (int axis = 0; axis < 3; ++axis) {
         const int n = p->dims[axis];
         if (n == 1) continue;
         int rad[CROFT_MAX_STAGES];
         int ns = factorize(n, rad, CROFT_MAX_STAGES);
-        if (ns < 1) { croft_plan_destroy(p); return CROFT_ERR_UNSUPPORTED_SIZE; }
+        if (ns < 1) return fail(p, CROFT_ERR_UNSUPPORTED_SIZE);
         std::vector<float> tw(2 * (size_t)(n - 1) + 2, 0.f);
-        if (build_twiddles(n, rad, ns, tw.data()) != n - 1) { croft_plan_destroy(p); return CROFT_ERR_UNSUPPORTED_SIZE; }
-        if (cudaMalloc((void**)&p->tw_dev[axis], sizeof(float2) * (size_t)n) != cudaSuccess) {
+        if (build_twiddles(n, rad, ns, tw.data()) != n - 1) return fail(p, CROFT_ERR_UNSUPPORTED_SIZE);
+        if (cudaMalloc((void**)&p->tw_dev[axis], sizeof(float2) * (size_t)n) != cudaSuccess) return fail(p, CROFT_ERR_OOM);
+        if (cudaMemcpy(p->tw_dev[axis], tw.data(), sizeof(float2) * (size_t)(n - 1), cudaMemcpyHostToDevice) != cudaSuccess)
+            return fail(p, CROFT_ERR_CUDA);
+    }
+
+    // schedule: fused yz-plane pass + x pass when a plane kernel exists for (ny, nz)
+    // and its cluster fits on this device, else one pass per axis (z, y, x)
+    const PlaneKernel* pk = (ny > 1 && nz > 1) ? find_plane_kernel(ny, nz) : NULL;
+    if (sched == CROFT_SCHEDULE_PLANE_FUSED && !pk) return fail(p, CROFT_ERR_UNSUPPORTED_SIZE);
+    bool fused = false;
+    if (pk && sched != CROFT_SCHEDULE_THREE_PASS) {
+        croft_status st = add_plane_pass(p, pk);
+        if (st == CROFT_OK) {
+            fused = true;
+        } else {
             cudaGetLastError();
-            croft_plan_destroy(p);
-            return CROFT_ERR_OOM;
+            p->passes.clear();
+            p->pass_axis.clear();
+            if (sched == CROFT_SCHEDULE_PLANE_FUSED) return fail(p, st);
         }
-        if (cudaMemcpy(p->tw_dev[axis], tw.data(), sizeof(float2) * (size_t)(n - 1), cudaMemcpyHostToDevice) != cudaSuccess) {
-            cudaGetLastError();
-            croft_plan_destroy(p);
-            return CROFT_ERR_CUDA;
-        }
-        // element stride of the axis; a unit stride means the pencils are contiguous rows
-        const long long M = (axis == 2) ? 1 : (axis == 1 ? (long long)nz : (long long)ny * nz);
-        PassLaunch L;
-        bool ok = shape_pass(L, M == 1 ? LAYOUT_ROW : LAYOUT_COL, n, M, N / n);
-        if (!ok) { croft_plan_destroy(p); return CROFT_ERR_UNSUPPORTED_SIZE; }
-        if (prepare_pass(L) != cudaSuccess) { cudaGetLastError(); croft_plan_destroy(p); return CROFT_ERR_CUDA; }
-        L.args.tw = p->tw_dev[axis];
-        p->passes.push_back(L);
-        p->pass_axis.push_back(axis);
+    }
+    const int axes_fused[1] = {0};
+    const int axes_all[3] = {2, 1, 0};
+    const int* axes = fused ? axes_fused : axes_all;
+    const int naxes = fused ? 1 : 3;
+    for (int i = 0; i < naxes; ++i) {
+        if (p->dims[axes[i]] == 1) continue;
+        croft_status st = add_axis_pass(p, axes[i]);
+        if (st != CROFT_OK) return fail(p, st);
     }
     const char* log = getenv("CROFT_LOG");
     if (log && log[0] == '1') {
-        char buf[1024];
+        char buf[2048];
         croft_plan_describe(p, buf, sizeof(buf));
         fprintf(stderr, "croft: %s\n", buf);
     }
     *out = p;
     return CROFT_OK;
+}
+
+croft_status croft_plan_create(croft_plan* out, int nx, int ny, int nz, croft_dtype dtype) {
+    return create_impl(out, nx, ny, nz, dtype, CROFT_SCHEDULE_AUTO);
+}
+
+croft_status croft_plan_create_schedule(croft_plan* out, int nx, int ny, int nz, croft_dtype dtype,
+                                        croft_schedule schedule) {
+    return create_impl(out, nx, ny, nz, dtype, schedule);
 }
 
 int croft_plan_describe(croft_plan plan, char* buf, int cap) {
@@ -253,6 +313,12 @@ int croft_plan_describe(croft_plan plan, char* buf, int cap) {
     static const char* an[3] = {"x", "y", "z"};
     for (size_t i = 0; i < plan->passes.size(); ++i) {
         const PassLaunch& L = plan->passes[i];
+        if (L.kind == PASS_PLANE) {
+            snprintf(tmp, sizeof(tmp), " | yz:plane %dx%d cluster=%d block=%d grid=%d smem=%d active_clusters=%d",
+                     L.pk.ny, L.pk.nz, L.pk.cluster, L.block, L.grid, L.smem, active_clusters(L));
+            s += tmp;
+            continue;
+        }
         snprintf(tmp, sizeof(tmp), " | %s:%s n=%d radix=", an[plan->pass_axis[i]], L.layout == LAYOUT_ROW ? "row" : "col",
                  L.args.n);
         s += tmp;
@@ -334,6 +400,7 @@ static croft_status exec_dir(croft_plan plan, const void* in, void* out, void* s
     for (size_t i = 0; i < plan->passes.size(); ++i) {
         PassLaunch L = plan->passes[i];
         L.args.isign = isign;
+        L.pargs.isign = isign;
         cudaError_t e = launch_pass(L, src, dst, s);
         if (e != cudaSuccess) { cudaGetLastError(); return CROFT_ERR_CUDA; }
         if (tm && cudaEventRecord(plan->ev[i + 1], s) != cudaSuccess) { cudaGetLastError(); return CROFT_ERR_CUDA; }

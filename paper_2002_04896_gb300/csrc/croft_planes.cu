@@ -1,0 +1,27 @@
+// croft_planes.cu - instantiations of the fused z+y plane kernel and their registry.
+//
+// One entry per (ny, nz) plane shape with the cluster size C chosen so that a
+// CTA's tile is ~64-140 KB and at most 1024 threads: every CTA holds NY/C rows
+// in the z phase and NZ/C columns in the y phase.  Other plane shapes run the
+// three-pass schedule.
+#include "croft_plane_kernel.cuh"
+
+namespace croft {
+
+#define CROFT_PLANE(NY, NZ, C)                                                                       \
+    {croft_plane_kernel<NY, NZ, C>, NY, NZ, C, PlaneShape<NY, NZ, C>::THREADS,                          \
+     PlaneShape<NY, NZ, C>::SMEM_BYTES}
+
+static const PlaneKernel kPlaneKernels[] = {
+    CROFT_PLANE(32, 32, 1),    CROFT_PLANE(64, 64, 1),    CROFT_PLANE(128, 128, 2),
+    CROFT_PLANE(256, 256, 8),  CROFT_PLANE(384, 384, 16), CROFT_PLANE(480, 480, 16),
+    CROFT_PLANE(512, 512, 16), CROFT_PLANE(360, 320, 8),
+};
+
+const PlaneKernel* find_plane_kernel(int ny, int nz) {
+    for (const PlaneKernel& k : kPlaneKernels)
+        if (k.ny == ny && k.nz == nz) return &k;
+    return nullptr;
+}
+
+}  // namespace croft

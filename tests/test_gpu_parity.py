@@ -154,3 +154,51 @@ def test_binding_rejects_non_contiguous_and_wrong_dtype(croft_lib, dev):
             p.forward(x.to(torch.complex128))
         with pytest.raises(ValueError):
             p.forward(torch.zeros((8, 6, 5), dtype=torch.complex64, device="cuda"))
+
+
+PLANE_SHAPES = [(32, 32), (64, 64), (128, 128), (256, 256), (384, 384), (480, 480), (512, 512), (360, 320)]
+
+
+@pytest.mark.parametrize("ny,nz", PLANE_SHAPES)
+def test_fused_plane_schedule_matches_oracle(croft_lib, dev, ny, nz):
+    """The fused yz-plane pass (cluster / DSMEM all-to-all) + x pass, forward and backward."""
+    shape = (3, ny, nz)
+    x = S.white_noise(shape, ny + nz)
+    d = torch.from_numpy(x).cuda()
+    with croft_lib.Plan(*shape, schedule=croft_lib.CROFT_SCHEDULE_PLANE_FUSED) as p:
+        desc = p.describe()
+        assert "yz:plane" in desc, desc
+        assert croft_lib.croft_plan_num_launches(p.handle) == 2
+        yf = p.forward(d)
+        yb = p.backward(d)
+        torch.cuda.synchronize()
+    ef = oracle.rel_l2(yf.cpu().numpy(), oracle.forward(x))
+    eb = oracle.rel_l2(yb.cpu().numpy(), oracle.backward(x))
+    print(f"fused {shape}: fwd {ef:.3e} bwd {eb:.3e}")
+    assert ef <= tol(shape) and eb <= tol(shape)
+
+
+@pytest.mark.parametrize("ny,nz", PLANE_SHAPES[:4])
+def test_fused_plane_only_no_x_axis(croft_lib, dev, ny, nz):
+    x = S.white_noise((1, ny, nz), 3)
+    y = run(croft_lib, x)
+    assert oracle.rel_l2(y, oracle.forward(x)) <= tol(x.shape)
+
+
+def test_schedules_agree_and_auto_prefers_fused(croft_lib, dev):
+    x = torch.from_numpy(S.white_noise((16, 256, 256), 9)).cuda()
+    with croft_lib.Plan(16, 256, 256) as pa, \
+            croft_lib.Plan(16, 256, 256, schedule=croft_lib.CROFT_SCHEDULE_THREE_PASS) as p3:
+        assert "yz:plane" in pa.describe()
+        assert croft_lib.croft_plan_num_launches(p3.handle) == 3
+        a = pa.forward(x)
+        b = p3.forward(x)
+        torch.cuda.synchronize()
+    assert oracle.rel_l2(a.cpu().numpy(), b.cpu().numpy()) <= tol((16, 256, 256))
+
+
+def test_fused_schedule_unavailable_shape(croft_lib, dev):
+    st, h = croft_lib.croft_plan_create_status(4, 48, 80, 0, croft_lib.CROFT_SCHEDULE_PLANE_FUSED)
+    assert st == croft_lib.CROFT_ERR_UNSUPPORTED_SIZE and h is None
+    st, h = croft_lib.croft_plan_create_status(4, 48, 80, 0, 9)
+    assert st == croft_lib.CROFT_ERR_INVALID_ARG and h is None
