@@ -240,7 +240,10 @@ def run_croft(args):
     l2 = torch.cuda.get_device_properties(dev).L2_cache_size
     flush = torch.empty(max(2 * l2, 1 << 30) // 4, dtype=torch.float32, device=dev)
 
-    plan = croft.Plan(*shape)
+    sched = {"auto": None, "three_pass": croft.CROFT_SCHEDULE_THREE_PASS,
+             "plane_fused": croft.CROFT_SCHEDULE_PLANE_FUSED}[args.schedule]
+    plan = croft.Plan(*shape, schedule=sched)
+    plan_desc = plan.describe()
     croft.croft_plan_set_timing(plan.handle, True)
     launches_per_step = 2 * croft.croft_plan_num_launches(plan.handle)
     sh = stream.cuda_stream
@@ -305,7 +308,7 @@ def run_croft(args):
     npass = len(rec[0][1])
     pass_ms = [statistics.mean([r[1][i] for r in rec] + [r[2][i] for r in rec]) for i in range(npass)]
     dom = max(range(npass), key=lambda i: pass_ms[i])
-    axis_names = ["z", "y", "x"][-npass:] if npass == 3 else [f"p{i}" for i in range(npass)]
+    axis_names = {3: ["z", "y", "x"], 2: ["yz", "x"], 1: ["yz"]}.get(npass, [f"p{i}" for i in range(npass)])
     peak, peak_kind = measured_peaks()
     alg_bytes = 16.0 * n_total  # one read + one write of the grid per pass launch
     achieved = alg_bytes / (pass_ms[dom] * 1e-3) / 1e9
@@ -361,7 +364,7 @@ def run_croft(args):
             "config": {"workload": WORKLOAD, "grid": list(shape), "direction": "forward+backward",
                        "l2": "flushed before every step (writes of a 1 GiB buffer, > 2x L2, outside the timed events)",
                        "parallelism": f"replicas x{world}" if world > 1 else "single GPU",
-                       "passes_per_direction": npass},
+                       "passes_per_direction": npass, "schedule": args.schedule, "plan": plan_desc},
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                          "frac": achieved / peak, "traffic": traffic, "kernel": dom_key,
                          "peak_source": peak_kind, "alg_bytes_per_launch": alg_bytes,
@@ -387,6 +390,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="croft", choices=["croft", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--schedule", default="auto", choices=["auto", "three_pass", "plane_fused"])
     ap.add_argument("--clock-window-s", type=float, default=2.0,
                     help="minimum wall time of the timed region, padded with untimed L2-flush writes "
                          "between steps (0 under a profiler)")
