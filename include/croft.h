@@ -87,8 +87,8 @@ croft_status croft_plan_create(croft_plan* out, int nx, int ny, int nz, croft_dt
  *       yz-plane, one plane per thread-block cluster, the column all-to-all
  *       done through distributed shared memory), then the x pass; the grid
  *       crosses HBM twice.  Available for the plane shapes the library
- *       instantiates (ny x nz in {32x32, 64x64, 128x128, 256x256, 384x384,
- *       480x480, 512x512, 360x320}); other shapes give CROFT_ERR_UNSUPPORTED_SIZE.
+ *       instantiates (ny x nz in {32x32, 64x64, 128x128, 256x256, 384x384});
+ *       other shapes give CROFT_ERR_UNSUPPORTED_SIZE.
  *   CROFT_SCHEDULE_AUTO : PLANE_FUSED when available, else THREE_PASS.
  */
 typedef enum {

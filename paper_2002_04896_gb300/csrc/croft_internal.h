@@ -55,7 +55,8 @@ struct PassLaunch {
 };
 
 // croft_planes.cu
-const PlaneKernel* find_plane_kernel(int ny, int nz);  // NULL if no fused kernel for this plane
+// fused kernel for an ny x nz plane with the given cluster size (<= 0: the default one); NULL if none
+const PlaneKernel* find_plane_kernel(int ny, int nz, int cluster);
 
 // croft_kernels.cu, one per size group
 pass_fn lookup_pass_kernel_group_0(int layout, int n);

@@ -261,7 +261,9 @@ static croft_status create_impl(croft_plan* out, int nx, int ny, int nz, croft_d
 
     // schedule: fused yz-plane pass + x pass when a plane kernel exists for (ny, nz)
     // and its cluster fits on this device, else one pass per axis (z, y, x)
-    const PlaneKernel* pk = (ny > 1 && nz > 1) ? find_plane_kernel(ny, nz) : NULL;
+    const char* envc = getenv("CROFT_PLANE_CLUSTER");
+    const int want_cluster = envc ? atoi(envc) : 0;
+    const PlaneKernel* pk = (ny > 1 && nz > 1) ? find_plane_kernel(ny, nz, want_cluster) : NULL;
     if (sched == CROFT_SCHEDULE_PLANE_FUSED && !pk) return fail(p, CROFT_ERR_UNSUPPORTED_SIZE);
     bool fused = false;
     if (pk && sched != CROFT_SCHEDULE_THREE_PASS) {

@@ -12,15 +12,16 @@ namespace croft {
     {croft_plane_kernel<NY, NZ, C>, NY, NZ, C, PlaneShape<NY, NZ, C>::THREADS,                          \
      PlaneShape<NY, NZ, C>::SMEM_BYTES}
 
+// Several cluster sizes per shape where they fit; the first entry is the default.
 static const PlaneKernel kPlaneKernels[] = {
-    CROFT_PLANE(32, 32, 1),    CROFT_PLANE(64, 64, 1),    CROFT_PLANE(128, 128, 2),
-    CROFT_PLANE(256, 256, 8),  CROFT_PLANE(384, 384, 16), CROFT_PLANE(480, 480, 16),
-    CROFT_PLANE(512, 512, 16), CROFT_PLANE(360, 320, 8),
+    CROFT_PLANE(32, 32, 1),     CROFT_PLANE(64, 64, 1),     CROFT_PLANE(128, 128, 4),
+    CROFT_PLANE(128, 128, 2),   CROFT_PLANE(256, 256, 16),  CROFT_PLANE(256, 256, 8),
+    CROFT_PLANE(384, 384, 16),
 };
 
-const PlaneKernel* find_plane_kernel(int ny, int nz) {
+const PlaneKernel* find_plane_kernel(int ny, int nz, int cluster) {
     for (const PlaneKernel& k : kPlaneKernels)
-        if (k.ny == ny && k.nz == nz) return &k;
+        if (k.ny == ny && k.nz == nz && (cluster <= 0 || k.cluster == cluster)) return &k;
     return nullptr;
 }
 

@@ -156,7 +156,7 @@ def test_binding_rejects_non_contiguous_and_wrong_dtype(croft_lib, dev):
             p.forward(torch.zeros((8, 6, 5), dtype=torch.complex64, device="cuda"))
 
 
-PLANE_SHAPES = [(32, 32), (64, 64), (128, 128), (256, 256), (384, 384), (480, 480), (512, 512), (360, 320)]
+PLANE_SHAPES = [(32, 32), (64, 64), (128, 128), (256, 256), (384, 384)]
 
 
 @pytest.mark.parametrize("ny,nz", PLANE_SHAPES)
