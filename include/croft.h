@@ -103,6 +103,71 @@ croft_status croft_plan_create_schedule(croft_plan* out, int nx, int ny, int nz,
                                         croft_schedule schedule);
 
 /*
+ * Batched form: `count` independent grids of (possibly) different shapes,
+ * e.g. the per-system PME meshes of an ensemble.  Each grid is transformed
+ * exactly as by a single-grid plan of its shape (Eq. 1 / Eq. 2 unnormalised,
+ * same layout rules); the grids share launches.
+ *
+ * croft_plan_create_batched_mode:
+ *   dims  : host array of 3*count ints, grid g is (dims[3g], dims[3g+1], dims[3g+2]).
+ *   mode  : CROFT_BATCH_ONE_LAUNCH - every tile of every pass of every grid in
+ *               one persistent kernel launch (work counter, per-grid pass
+ *               dependencies as bounded device-side waits); recorded in a CUDA
+ *               graph per direction.
+ *           CROFT_BATCH_PER_PASS  - the same work in three persistent launches
+ *               (z, y, x), ordered by kernel boundaries; CUDA graph per direction.
+ *           CROFT_BATCH_PER_GRID  - one single-grid plan per grid, launched in turn.
+ *           CROFT_BATCH_AUTO      - time the three on scratch buffers at creation
+ *               and keep the fastest; the choice is cached in the text file named
+ *               by $CROFT_TUNE_CACHE (default $HOME/.croft_tune_cache.txt), keyed by
+ *               the sizes, GPU name and CUDA runtime version.  CROFT_TUNE=off skips
+ *               the timing and uses ONE_LAUNCH.
+ *   Grids with an axis > 128 always run on their own single-grid plan.
+ * croft_plan_create_batched: the same with CROFT_BATCH_AUTO.
+ * Paper: many 1D FFTs under one plan ("option 4") and the chunk count K
+ * trading call count against chunk size (Sec. 5.1).
+ * Returns CROFT_OK, CROFT_ERR_INVALID_ARG (count < 1, NULL dims/out, bad mode
+ * or dtype), CROFT_ERR_UNSUPPORTED_SIZE (an axis, or the tensor-core dtype),
+ * CROFT_ERR_OOM or CROFT_ERR_CUDA.  The plan owns a small device workspace
+ * (work counters, per-grid completion counts, status word) and pinned host
+ * memory for the grids' descriptors.
+ */
+typedef enum {
+    CROFT_BATCH_AUTO = 0,
+    CROFT_BATCH_ONE_LAUNCH = 1,
+    CROFT_BATCH_PER_PASS = 2,
+    CROFT_BATCH_PER_GRID = 3
+} croft_batch_mode;
+
+croft_status croft_plan_create_batched(croft_plan* out, int count, const int* dims, croft_dtype dtype);
+croft_status croft_plan_create_batched_mode(croft_plan* out, int count, const int* dims, croft_dtype dtype,
+                                            croft_batch_mode mode);
+
+/*
+ * croft_exec_batched_forward / _backward: in and out are HOST arrays of
+ * `count` DEVICE pointers (grid g reads in[g], writes out[g]); each pair obeys
+ * the single-grid rules (16-byte aligned, in[g] == out[g] or disjoint).
+ * Stream-ordered.  The grids' descriptors travel through pinned host memory
+ * owned by the plan, so an exec first waits (on the host) until the previous
+ * exec of the same plan has started executing on the device.
+ * Device-side waits that run out set the plan's device status to
+ * CROFT_ERR_TIMEOUT (croft_plan_last_device_status); the exec itself still
+ * returns CROFT_OK in that case because it does not synchronise.
+ */
+croft_status croft_exec_batched_forward(croft_plan plan, void* const* in, void* const* out, void* stream);
+croft_status croft_exec_batched_backward(croft_plan plan, void* const* in, void* const* out, void* stream);
+
+/* Budget, in SM clock cycles, of each bounded device-side wait of a batched
+ * plan (default 4e9, about two seconds).  No effect on single-grid plans. */
+croft_status croft_plan_set_wait_limit(croft_plan plan, long long cycles);
+
+/* Test hook for the failure path: when enabled, the y-pass tiles of grid 0
+ * wait for one more finished z tile than grid 0 has, a count nothing ever
+ * reaches, so their waits run out after the wait limit and the plan reports
+ * CROFT_ERR_TIMEOUT.  ONE_LAUNCH schedule only.  Never hangs the GPU. */
+croft_status croft_plan_set_test_unsatisfiable_wait(croft_plan plan, int enable);
+
+/*
  * croft_exec_forward - Eq. (1), unnormalised, out = F(in).
  * croft_exec_backward - Eq. (2) with exponent +, WITHOUT the 1/N factor.
  *
@@ -115,7 +180,8 @@ croft_status croft_plan_create_schedule(croft_plan* out, int nx, int ny, int nz,
 croft_status croft_exec_forward(croft_plan plan, const void* in, void* out, void* stream);
 croft_status croft_exec_backward(croft_plan plan, const void* in, void* out, void* stream);
 
-/* Device scratch bytes held by the plan (0 when every pass runs in place). */
+/* Device scratch bytes held by the plan (0 when every pass runs in place;
+ * batched plans: their counters and status word). */
 size_t croft_plan_workspace_bytes(croft_plan plan);
 
 /* Number of kernel launches one exec of this plan issues. */

@@ -24,6 +24,11 @@ CROFT_SCHEDULE_AUTO = 0
 CROFT_SCHEDULE_THREE_PASS = 1
 CROFT_SCHEDULE_PLANE_FUSED = 2
 
+CROFT_BATCH_AUTO = 0
+CROFT_BATCH_ONE_LAUNCH = 1
+CROFT_BATCH_PER_PASS = 2
+CROFT_BATCH_PER_GRID = 3
+
 CROFT_OK = 0
 CROFT_ERR_INVALID_ARG = 1
 CROFT_ERR_UNSUPPORTED_SIZE = 2
@@ -55,6 +60,13 @@ _pass_times = _sig("croft_plan_pass_times", _I, [_P, ctypes.POINTER(ctypes.c_flo
 _last_device_status = _sig("croft_plan_last_device_status", _I, [_P])
 _plan_destroy = _sig("croft_plan_destroy", _I, [_P])
 _factorize = _sig("croft_factorize", _I, [_I, ctypes.POINTER(_I), _I])
+_plan_create_batched = _sig("croft_plan_create_batched", _I, [ctypes.POINTER(_P), _I, ctypes.POINTER(_I), _I])
+_plan_create_batched_mode = _sig("croft_plan_create_batched_mode", _I,
+                                 [ctypes.POINTER(_P), _I, ctypes.POINTER(_I), _I, _I])
+_exec_batched_forward = _sig("croft_exec_batched_forward", _I, [_P, ctypes.POINTER(_P), ctypes.POINTER(_P), _P])
+_exec_batched_backward = _sig("croft_exec_batched_backward", _I, [_P, ctypes.POINTER(_P), ctypes.POINTER(_P), _P])
+_set_wait_limit = _sig("croft_plan_set_wait_limit", _I, [_P, ctypes.c_longlong])
+_set_test_unsat = _sig("croft_plan_set_test_unsatisfiable_wait", _I, [_P, _I])
 _twiddle_table = _sig("croft_twiddle_table", _I, [_I, ctypes.POINTER(_I), _I, ctypes.POINTER(ctypes.c_float)])
 
 LIBRARY_PATH = _LIB_PATH
@@ -62,7 +74,9 @@ EXPORTED = [
     "croft_status_string", "croft_plan_create", "croft_plan_create_schedule", "croft_exec_forward", "croft_exec_backward",
     "croft_plan_workspace_bytes", "croft_plan_num_launches", "croft_plan_describe", "croft_plan_set_timing",
     "croft_plan_pass_times", "croft_plan_last_device_status", "croft_plan_destroy", "croft_factorize",
-    "croft_twiddle_table",
+    "croft_twiddle_table", "croft_plan_create_batched", "croft_plan_create_batched_mode",
+    "croft_exec_batched_forward", "croft_exec_batched_backward", "croft_plan_set_wait_limit",
+    "croft_plan_set_test_unsatisfiable_wait",
 ]
 
 
@@ -207,6 +221,109 @@ def croft_twiddle_table(n: int, radices):
     if k < 0:
         return None
     return out[: 2 * k].view(np.complex64)
+
+
+# ---------------------------------------------------------------------------
+# batched form
+# ---------------------------------------------------------------------------
+
+def croft_plan_create_batched_status(dims, dtype: int = CROFT_C2C_F32, mode=None):
+    flat = [int(v) for d in dims for v in d]
+    arr = (_I * max(1, len(flat)))(*flat)
+    h = _P()
+    if mode is None:
+        st = _plan_create_batched(ctypes.byref(h), len(dims), arr, int(dtype))
+    else:
+        st = _plan_create_batched_mode(ctypes.byref(h), len(dims), arr, int(dtype), int(mode))
+    return st, h.value
+
+
+def croft_plan_create_batched(dims, dtype: int = CROFT_C2C_F32, mode=None) -> int:
+    st, h = croft_plan_create_batched_status(dims, dtype, mode)
+    _check(st, f"croft_plan_create_batched({len(dims)} grids, mode={mode})")
+    return h
+
+
+def _ptr_array(xs, sizes=None):
+    vals = [_ptr(x, None if sizes is None else sizes[i]) for i, x in enumerate(xs)]
+    return (_P * max(1, len(vals)))(*vals)
+
+
+def croft_exec_batched_forward_status(plan: int, ins, outs, stream=None) -> int:
+    return _exec_batched_forward(plan, _ptr_array(ins), _ptr_array(outs), _stream_ptr(stream))
+
+
+def croft_exec_batched_backward_status(plan: int, ins, outs, stream=None) -> int:
+    return _exec_batched_backward(plan, _ptr_array(ins), _ptr_array(outs), _stream_ptr(stream))
+
+
+def croft_exec_batched_forward(plan: int, ins, outs, stream=None) -> None:
+    _check(croft_exec_batched_forward_status(plan, ins, outs, stream), "croft_exec_batched_forward")
+
+
+def croft_exec_batched_backward(plan: int, ins, outs, stream=None) -> None:
+    _check(croft_exec_batched_backward_status(plan, ins, outs, stream), "croft_exec_batched_backward")
+
+
+def croft_plan_set_wait_limit(plan: int, cycles: int) -> None:
+    _check(_set_wait_limit(plan, int(cycles)), "croft_plan_set_wait_limit")
+
+
+def croft_plan_set_test_unsatisfiable_wait(plan: int, enable: bool) -> None:
+    _check(_set_test_unsat(plan, 1 if enable else 0), "croft_plan_set_test_unsatisfiable_wait")
+
+
+class BatchPlan:
+    """RAII helper around a batched plan: lists of torch tensors in and out."""
+
+    def __init__(self, dims, dtype: int = CROFT_C2C_F32, mode=None):
+        self.dims = [tuple(int(v) for v in d) for d in dims]
+        self.handle = None
+        self.handle = croft_plan_create_batched(self.dims, dtype, mode)
+
+    def _check_lists(self, ins, outs):
+        if len(ins) != len(self.dims) or len(outs) != len(self.dims):
+            raise ValueError("one input and one output per grid")
+        for d, a, b in zip(self.dims, ins, outs):
+            n = d[0] * d[1] * d[2]
+            _ptr(a, n)
+            _ptr(b, n)
+
+    def forward(self, ins, outs=None, stream=None):
+        import torch
+        if outs is None:
+            outs = [torch.empty(d, dtype=torch.complex64, device=x.device) for d, x in zip(self.dims, ins)]
+        self._check_lists(ins, outs)
+        croft_exec_batched_forward(self.handle, ins, outs, stream)
+        return outs
+
+    def backward(self, ins, outs=None, stream=None):
+        import torch
+        if outs is None:
+            outs = [torch.empty(d, dtype=torch.complex64, device=x.device) for d, x in zip(self.dims, ins)]
+        self._check_lists(ins, outs)
+        croft_exec_batched_backward(self.handle, ins, outs, stream)
+        return outs
+
+    def describe(self) -> str:
+        return croft_plan_describe(self.handle)
+
+    def close(self):
+        if self.handle:
+            croft_plan_destroy(self.handle)
+            self.handle = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:  # noqa: BLE001
+            pass
 
 
 class Plan:

@@ -44,6 +44,18 @@ struct GlobalInUnit {  // unit stride (contiguous pencil)
         return t;
     }
 };
+// As GlobalIn, but read through L2 only (ld.global.cg): for data another CTA
+// wrote earlier in the same launch (the batched persistent kernel).
+struct GlobalInCG {
+    const float2* p;
+    long long stride;
+    float isign;
+    __device__ __forceinline__ float2 load(int a) const {
+        float2 t = __ldcg(p + (long long)a * stride);
+        t.y *= isign;
+        return t;
+    }
+};
 struct GlobalOut {
     float2* p;
     long long stride;

@@ -18,21 +18,9 @@
 
 #include "../../include/croft.h"
 #include "croft_internal.h"
+#include "croft_plan_internal.h"
 
 using namespace croft;
-
-struct croft_plan_s {
-    int dims[3];          // nx, ny, nz
-    croft_dtype dtype;
-    int device;
-    std::vector<PassLaunch> passes;   // execution order (z, y, x; length-1 axes skipped)
-    std::vector<int> pass_axis;       // axis index of each pass (2 = z, 1 = y, 0 = x)
-    float2* tw_dev[3];                // per-axis twiddle tables (NULL for length <= 1)
-    bool timing;
-    cudaEvent_t ev[4];
-    int ev_count;                     // events recorded by the last exec
-    bool ran;
-};
 
 // ---------------------------------------------------------------------------
 // host planning helpers
@@ -90,6 +78,21 @@ static int build_twiddles(int n, const int* radices, int ns, float* out) {
     }
     return p == n ? n - 1 : -1;
 }
+
+namespace croft {
+// twiddle table of a length-n axis in the library's schedule (n-1 entries); used by batched plans
+int host_build_twiddles(int n, float* out) {
+    int rad[CROFT_MAX_STAGES];
+    const int ns = factorize(n, rad, CROFT_MAX_STAGES);
+    if (ns < 1) return -1;
+    return build_twiddles(n, rad, ns, out);
+}
+int batch_plan_mode(const croft_plan_s* p);
+croft_status batch_last_status(croft_plan_s* p);
+size_t batch_workspace_bytes(const croft_plan_s* p);
+int batch_num_launches(const croft_plan_s* p);
+std::string batch_describe(const croft_plan_s* p);
+}  // namespace croft
 
 static int g_max_smem = 0;
 
@@ -169,6 +172,7 @@ croft_status croft_plan_destroy(croft_plan plan) {
         if (plan->tw_dev[a]) cudaFree(plan->tw_dev[a]);
     for (int i = 0; i < 4; ++i)
         if (plan->ev[i]) cudaEventDestroy(plan->ev[i]);
+    if (plan->batch) batch_state_destroy(plan->batch);
     if (cur >= 0) cudaSetDevice(cur);
     delete plan;
     return CROFT_OK;
@@ -244,6 +248,7 @@ static croft_status create_impl(croft_plan* out, int nx, int ny, int nz, croft_d
     p->timing = false;
     p->ev_count = 0;
     p->ran = false;
+    p->batch = NULL;
 
     // twiddle tables, one per axis of length > 1
     for (int axis = 0; axis < 3; ++axis) {
@@ -309,6 +314,8 @@ int croft_plan_describe(croft_plan plan, char* buf, int cap) {
     if (!plan) return -1;
     std::string s;
     char tmp[256];
+    if (plan->batch) s = batch_describe(plan);
+    else {
     snprintf(tmp, sizeof(tmp), "grid %dx%dx%d dtype %d passes %d", plan->dims[0], plan->dims[1], plan->dims[2],
              (int)plan->dtype, (int)plan->passes.size());
     s += tmp;
@@ -332,6 +339,7 @@ int croft_plan_describe(croft_plan plan, char* buf, int cap) {
         snprintf(tmp, sizeof(tmp), " T=%d W=%d block=%d grid=%d smem=%d", L.T, L.args.W, L.block, L.grid, L.smem);
         s += tmp;
     }
+    }
     if (buf && cap > 0) {
         size_t m = s.size() < (size_t)(cap - 1) ? s.size() : (size_t)(cap - 1);
         memcpy(buf, s.data(), m);
@@ -341,12 +349,13 @@ int croft_plan_describe(croft_plan plan, char* buf, int cap) {
 }
 
 size_t croft_plan_workspace_bytes(croft_plan plan) {
-    (void)plan;
+    if (plan && plan->batch) return batch_workspace_bytes(plan);
     return 0;
 }
 
 int croft_plan_num_launches(croft_plan plan) {
     if (!plan) return -1;
+    if (plan->batch) return batch_num_launches(plan);
     return plan->passes.empty() ? 0 : (int)plan->passes.size();
 }
 
@@ -375,11 +384,12 @@ int croft_plan_pass_times(croft_plan plan, float* ms, int cap) {
 
 croft_status croft_plan_last_device_status(croft_plan plan) {
     if (!plan) return CROFT_ERR_INVALID_ARG;
+    if (plan->batch) return batch_last_status(plan);
     return CROFT_OK;
 }
 
 static croft_status exec_dir(croft_plan plan, const void* in, void* out, void* stream, float isign) {
-    if (!plan || !in || !out) return CROFT_ERR_INVALID_ARG;
+    if (!plan || !in || !out || plan->batch) return CROFT_ERR_INVALID_ARG;
     if (((uintptr_t)in & 15) || ((uintptr_t)out & 15)) return CROFT_ERR_INVALID_ARG;
     const long long N = (long long)plan->dims[0] * plan->dims[1] * plan->dims[2];
     const size_t bytes = (size_t)N * sizeof(float2);

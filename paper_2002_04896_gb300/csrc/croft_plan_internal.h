@@ -1,0 +1,28 @@
+// croft_plan_internal.h - the plan object behind the opaque croft_plan handle.
+#pragma once
+#include <cuda_runtime.h>
+
+#include <vector>
+
+#include "../../include/croft.h"
+#include "croft_internal.h"
+
+namespace croft {
+struct BatchState;  // croft_batch_plan.cu
+void batch_state_destroy(BatchState* b);
+}  // namespace croft
+
+struct croft_plan_s {
+    int dims[3];          // nx, ny, nz
+    croft_dtype dtype;
+    int device;
+    std::vector<croft::PassLaunch> passes;   // execution order (z, y, x; length-1 axes skipped)
+    std::vector<int> pass_axis;       // axis index of each pass (2 = z, 1 = y, 0 = x)
+    float2* tw_dev[3];                // per-axis twiddle tables (NULL for length <= 1)
+    bool timing;
+    cudaEvent_t ev[4];
+    int ev_count;                     // events recorded by the last exec
+    bool ran;
+    croft::BatchState* batch;         // batched plans only (NULL for a single-grid plan)
+};
+
