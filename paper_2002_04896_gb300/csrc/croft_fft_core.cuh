@@ -101,12 +101,27 @@ struct CtaBarrier {
 };
 
 // ---------------------------------------------------------------------------
+// schedules (which radix each stage of a length-N transform uses)
+// ---------------------------------------------------------------------------
+template <int N_>
+struct DefaultSched {
+    static constexpr int N = N_;
+    __host__ __device__ static constexpr CroftSched get() { return croft_make_sched(N_); }
+};
+template <int N_>
+struct Tc16Sched {
+    static constexpr int N = N_;
+    __host__ __device__ static constexpr CroftSched get() { return croft_make_sched_tc(N_); }
+};
+
+// ---------------------------------------------------------------------------
 // the stage
 // ---------------------------------------------------------------------------
-template <int N, int S, int T, class Src, class Mid, class Dst>
-__device__ __forceinline__ void fft_stage(const Src& src, const Mid& mid, const Dst& dst, const float2* stw, int lane,
-                                          bool ok) {
-    constexpr CroftSched sc = croft_make_sched(N);
+template <class SchedT, int S, int T, class Src, class Mid, class Dst>
+__device__ __forceinline__ void fft_stage_s(const Src& src, const Mid& mid, const Dst& dst, const float2* stw,
+                                            int lane, bool ok) {
+    constexpr int N = SchedT::N;
+    constexpr CroftSched sc = SchedT::get();
     constexpr int R = sc.r[S];
     constexpr int P = croft_sched_p(sc, S);
     constexpr int NB = N / R;
@@ -137,6 +152,12 @@ __device__ __forceinline__ void fft_stage(const Src& src, const Mid& mid, const 
             for (int j = 0; j < R; ++j) dst.store(o + j * P, v[q][j]);
         }
     }
+}
+
+template <int N, int S, int T, class Src, class Mid, class Dst>
+__device__ __forceinline__ void fft_stage(const Src& src, const Mid& mid, const Dst& dst, const float2* stw, int lane,
+                                          bool ok) {
+    fft_stage_s<DefaultSched<N>, S, T>(src, mid, dst, stw, lane, ok);
 }
 
 // Stages [S, E) of a length-N FFT entirely in shared memory (in place), each

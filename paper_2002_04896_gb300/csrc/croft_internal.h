@@ -23,6 +23,8 @@ struct PassArgs {
     int W;              // pencils per CTA
     int tw_pad;         // float2 slots reserved for twiddles in shared memory
     float isign;        // +1 forward, -1 backward (conj-in / conj-out)
+    const unsigned char* tc_b;  // tensor-core passes: 16-point DFT matrix, bf16 hi | lo, core-matrix layout (4 KB)
+    int* status;                // tensor-core passes: device status word (bounded waits), may be null
 };
 
 // Fused z+y pass: 2D FFT of every yz-plane (one plane per cluster of C CTAs).
@@ -48,6 +50,7 @@ struct PassLaunch {
     PlaneArgs pargs;    // PASS_PLANE
     PlaneKernel pk;     // PASS_PLANE
     int layout;
+    int tc;             // 1: tensor-core variant of the pass kernel
     int T;              // threads per pencil (fixed by the kernel: croft_threads_per_pencil)
     int grid;
     int block;
@@ -63,6 +66,10 @@ pass_fn lookup_pass_kernel_group_0(int layout, int n);
 pass_fn lookup_pass_kernel_group_1(int layout, int n);
 pass_fn lookup_pass_kernel_group_2(int layout, int n);
 pass_fn lookup_pass_kernel_group_3(int layout, int n);
+
+// croft_tc.cu: tensor-core pass kernels (NULL when n has no instantiation)
+pass_fn tc_pass_kernel_for(int layout, int n);
+void tc_dft16_matrix(unsigned char* out4096);  // B operand (hi | lo) in the kernels' smem layout
 
 // croft_passes.cu
 pass_fn pass_kernel_for(int layout, int n);

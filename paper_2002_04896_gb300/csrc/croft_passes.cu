@@ -42,7 +42,7 @@ cudaError_t prepare_pass(const PassLaunch& L) {
         if (e != cudaSuccess) return e;
         return nclusters > 0 ? cudaSuccess : cudaErrorInvalidConfiguration;
     }
-    pass_fn f = pass_kernel_for(L.layout, L.args.n);
+    pass_fn f = L.tc ? tc_pass_kernel_for(L.layout, L.args.n) : pass_kernel_for(L.layout, L.args.n);
     if (!f) return cudaErrorInvalidValue;
     if (L.smem <= 48 * 1024) return cudaSuccess;
     return cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, L.smem);
@@ -54,7 +54,7 @@ cudaError_t launch_pass(const PassLaunch& L, const float2* in, float2* out, cuda
         cudaLaunchConfig_t cfg = plane_config(L, s, attr);
         return cudaLaunchKernelEx(&cfg, L.pk.fn, in, out, L.pargs);
     }
-    pass_fn f = pass_kernel_for(L.layout, L.args.n);
+    pass_fn f = L.tc ? tc_pass_kernel_for(L.layout, L.args.n) : pass_kernel_for(L.layout, L.args.n);
     if (!f) return cudaErrorInvalidValue;
     f<<<L.grid, L.block, L.smem, s>>>(in, out, L.args);
     return cudaGetLastError();

@@ -101,9 +101,10 @@ static int g_max_smem = 0;
 // COL: W adjacent columns per CTA, W a multiple of 16 (128-byte rows).
 // Aim for ~256 threads per CTA and <= 100 KB of shared memory so that at
 // least two CTAs share an SM.
-static bool shape_pass(PassLaunch& L, int layout, int n, long long M, long long ncols) {
+static bool shape_pass(PassLaunch& L, int layout, int n, long long M, long long ncols, bool tc = false) {
     memset(&L, 0, sizeof(L));
     L.layout = layout;
+    L.tc = tc ? 1 : 0;
     PassArgs& A = L.args;
     A.n = n;
     A.M = M;
@@ -128,8 +129,10 @@ static bool shape_pass(PassLaunch& L, int layout, int n, long long M, long long 
         A.W = W;
         L.smem = (int)((A.tw_pad + (long long)n * W) * 8);
     }
-    if (croft_make_sched(n).count <= 1) L.smem = 0;  // single-stage kernels touch no shared memory
+    if (croft_make_sched(n).count <= 1 && !tc) L.smem = 0;  // single-stage kernels touch no shared memory
+    if (tc) L.smem += 4096;                                  // + the DFT-16 operand
     L.block = A.W * T;
+    if (tc && (L.block % 128) != 0) return false;           // 128-butterfly GEMM groups
     if (L.block > max_threads) return false;
     long long grid = (ncols + A.W - 1) / A.W;
     if (grid > 0x7fffffffLL) return false;
@@ -173,6 +176,8 @@ croft_status croft_plan_destroy(croft_plan plan) {
     for (int i = 0; i < 4; ++i)
         if (plan->ev[i]) cudaEventDestroy(plan->ev[i]);
     if (plan->batch) batch_state_destroy(plan->batch);
+    if (plan->tc_b) cudaFree(plan->tc_b);
+    if (plan->d_status) cudaFree(plan->d_status);
     if (cur >= 0) cudaSetDevice(cur);
     delete plan;
     return CROFT_OK;
@@ -192,9 +197,11 @@ static croft_status add_axis_pass(croft_plan p, int axis) {
     // element stride of the axis; a unit stride means the pencils are contiguous rows
     const long long M = (axis == 2) ? 1 : (axis == 1 ? (long long)nz : (long long)ny * nz);
     PassLaunch L;
-    if (!shape_pass(L, M == 1 ? LAYOUT_ROW : LAYOUT_COL, n, M, N / n)) return CROFT_ERR_UNSUPPORTED_SIZE;
+    if (!shape_pass(L, M == 1 ? LAYOUT_ROW : LAYOUT_COL, n, M, N / n, p->axis_tc[axis])) return CROFT_ERR_UNSUPPORTED_SIZE;
     L.kind = PASS_AXIS;
     L.args.tw = p->tw_dev[axis];
+    L.args.tc_b = p->tc_b;
+    L.args.status = p->d_status;
     if (prepare_pass(L) != cudaSuccess) return CROFT_ERR_CUDA;
     p->passes.push_back(L);
     p->pass_axis.push_back(axis);
@@ -227,7 +234,6 @@ static croft_status create_impl(croft_plan* out, int nx, int ny, int nz, croft_d
     if (sched != CROFT_SCHEDULE_AUTO && sched != CROFT_SCHEDULE_THREE_PASS && sched != CROFT_SCHEDULE_PLANE_FUSED)
         return CROFT_ERR_INVALID_ARG;
     if (!axis_supported(nx) || !axis_supported(ny) || !axis_supported(nz)) return CROFT_ERR_UNSUPPORTED_SIZE;
-    if (dtype == CROFT_C2C_F32_TC_BF16X3) return CROFT_ERR_UNSUPPORTED_SIZE;  // enabled with the tensor-core stage
 
     int dev = 0;
     if (cudaGetDevice(&dev) != cudaSuccess) { cudaGetLastError(); return CROFT_ERR_CUDA; }
@@ -249,13 +255,35 @@ static croft_status create_impl(croft_plan* out, int nx, int ny, int nz, croft_d
     p->ev_count = 0;
     p->ran = false;
     p->batch = NULL;
+    p->tc_b = NULL;
+    p->d_status = NULL;
+    const bool want_tc = dtype == CROFT_C2C_F32_TC_BF16X3;
+    for (int axis = 0; axis < 3; ++axis) {
+        const long long M = (axis == 2) ? 1 : (axis == 1 ? (long long)nz : (long long)ny * nz);
+        p->axis_tc[axis] = want_tc && tc_pass_kernel_for(M == 1 ? LAYOUT_ROW : LAYOUT_COL, p->dims[axis]) != NULL;
+    }
+    if (want_tc) {
+        unsigned char hb[4096];
+        tc_dft16_matrix(hb);
+        if (cudaMalloc((void**)&p->tc_b, 4096) != cudaSuccess) return fail(p, CROFT_ERR_OOM);
+        if (cudaMalloc((void**)&p->d_status, sizeof(int)) != cudaSuccess) return fail(p, CROFT_ERR_OOM);
+        if (cudaMemcpy(p->tc_b, hb, 4096, cudaMemcpyHostToDevice) != cudaSuccess) return fail(p, CROFT_ERR_CUDA);
+        if (cudaMemset(p->d_status, 0, sizeof(int)) != cudaSuccess) return fail(p, CROFT_ERR_CUDA);
+    }
 
-    // twiddle tables, one per axis of length > 1
+    // twiddle tables, one per axis of length > 1 (tensor-core axes: radix-16-first schedule)
     for (int axis = 0; axis < 3; ++axis) {
         const int n = p->dims[axis];
         if (n == 1) continue;
         int rad[CROFT_MAX_STAGES];
-        int ns = factorize(n, rad, CROFT_MAX_STAGES);
+        int ns;
+        if (p->axis_tc[axis]) {
+            const CroftSched sc = croft_make_sched_tc(n);
+            ns = sc.count;
+            for (int i = 0; i < ns; ++i) rad[i] = sc.r[i];
+        } else {
+            ns = factorize(n, rad, CROFT_MAX_STAGES);
+        }
         if (ns < 1) return fail(p, CROFT_ERR_UNSUPPORTED_SIZE);
         std::vector<float> tw(2 * (size_t)(n - 1) + 2, 0.f);
         if (build_twiddles(n, rad, ns, tw.data()) != n - 1) return fail(p, CROFT_ERR_UNSUPPORTED_SIZE);
@@ -268,7 +296,7 @@ static croft_status create_impl(croft_plan* out, int nx, int ny, int nz, croft_d
     // and its cluster fits on this device, else one pass per axis (z, y, x)
     const char* envc = getenv("CROFT_PLANE_CLUSTER");
     const int want_cluster = envc ? atoi(envc) : 0;
-    const PlaneKernel* pk = (ny > 1 && nz > 1) ? find_plane_kernel(ny, nz, want_cluster) : NULL;
+    const PlaneKernel* pk = (ny > 1 && nz > 1 && !want_tc) ? find_plane_kernel(ny, nz, want_cluster) : NULL;
     if (sched == CROFT_SCHEDULE_PLANE_FUSED && !pk) return fail(p, CROFT_ERR_UNSUPPORTED_SIZE);
     bool fused = false;
     if (pk && sched != CROFT_SCHEDULE_THREE_PASS) {
@@ -328,10 +356,10 @@ int croft_plan_describe(croft_plan plan, char* buf, int cap) {
             s += tmp;
             continue;
         }
-        snprintf(tmp, sizeof(tmp), " | %s:%s n=%d radix=", an[plan->pass_axis[i]], L.layout == LAYOUT_ROW ? "row" : "col",
-                 L.args.n);
+        snprintf(tmp, sizeof(tmp), " | %s:%s%s n=%d radix=", an[plan->pass_axis[i]], L.layout == LAYOUT_ROW ? "row" : "col",
+                 L.tc ? "+tc" : "", L.args.n);
         s += tmp;
-        CroftSched sc = croft_make_sched(L.args.n);
+        CroftSched sc = L.tc ? croft_make_sched_tc(L.args.n) : croft_make_sched(L.args.n);
         for (int st = 0; st < sc.count; ++st) {
             snprintf(tmp, sizeof(tmp), "%s%d", st ? "x" : "", sc.r[st]);
             s += tmp;
@@ -385,6 +413,14 @@ int croft_plan_pass_times(croft_plan plan, float* ms, int cap) {
 croft_status croft_plan_last_device_status(croft_plan plan) {
     if (!plan) return CROFT_ERR_INVALID_ARG;
     if (plan->batch) return batch_last_status(plan);
+    if (plan->d_status) {
+        int st = 0;
+        if (cudaMemcpy(&st, plan->d_status, sizeof(int), cudaMemcpyDeviceToHost) != cudaSuccess) {
+            cudaGetLastError();
+            return CROFT_ERR_CUDA;
+        }
+        return st == 0 ? CROFT_OK : (croft_status)st;
+    }
     return CROFT_OK;
 }
 
@@ -406,6 +442,10 @@ static croft_status exec_dir(croft_plan plan, const void* in, void* out, void* s
         return CROFT_OK;
     }
     const bool tm = plan->timing;
+    if (plan->d_status && cudaMemsetAsync(plan->d_status, 0, sizeof(int), s) != cudaSuccess) {
+        cudaGetLastError();
+        return CROFT_ERR_CUDA;
+    }
     if (tm && cudaEventRecord(plan->ev[0], s) != cudaSuccess) { cudaGetLastError(); return CROFT_ERR_CUDA; }
     const float2* src = (const float2*)in;
     float2* dst = (float2*)out;

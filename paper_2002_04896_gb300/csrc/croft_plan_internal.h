@@ -24,5 +24,8 @@ struct croft_plan_s {
     int ev_count;                     // events recorded by the last exec
     bool ran;
     croft::BatchState* batch;         // batched plans only (NULL for a single-grid plan)
+    unsigned char* tc_b;              // tensor-core plans: DFT-16 operand (4 KB), else NULL
+    int* d_status;                    // tensor-core plans: device status word, else NULL
+    bool axis_tc[3];                  // axis runs the tensor-core pass kernel
 };
 

@@ -47,6 +47,25 @@ CROFT_HD constexpr CroftSched croft_make_sched(int n) {
     return s;
 }
 
+// Schedule of the tensor-core variant: as many radix-16 stages as n has factors
+// of 16 (these run as split-bf16 GEMMs), then the ordinary schedule of the rest.
+CROFT_HD constexpr CroftSched croft_make_sched_tc(int n) {
+    CroftSched s{0, {0, 0, 0, 0, 0, 0, 0, 0}};
+    int m = n, k = 0;
+    while (m > 1 && m % 16 == 0 && k < CROFT_MAX_STAGES) {
+        s.r[k++] = 16;
+        m /= 16;
+    }
+    const CroftSched rest = croft_make_sched(m);
+    if (rest.count < 0 || k + rest.count > CROFT_MAX_STAGES) {
+        s.count = -1;
+        return s;
+    }
+    for (int i = 0; i < rest.count; ++i) s.r[k++] = rest.r[i];
+    s.count = k;
+    return s;
+}
+
 // Length of the sub-transforms that stage `stage` combines (product of the earlier radices).
 CROFT_HD constexpr int croft_sched_p(const CroftSched& s, int stage) {
     int p = 1;
