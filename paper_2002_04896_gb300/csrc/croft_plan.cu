@@ -119,7 +119,7 @@ static bool shape_pass(PassLaunch& L, int layout, int n, long long M, long long 
         int W = (256 + T - 1) / T;
         if (W < 1) W = 1;
         while (W > 1 && (W * T > max_threads || (A.tw_pad + (long long)W * ld) * 8 > smem_cap)) --W;
-        if ((long long)W > ncols) W = (int)ncols;
+        if ((long long)W > ncols && !tc) W = (int)ncols;  // (tensor-core tiles keep whole 128-row groups)
         A.W = W;
         L.smem = (int)((A.tw_pad + (long long)W * ld) * 8);
     } else {
