@@ -88,36 +88,42 @@ void batch_state_destroy(BatchState* b) {
 }
 
 static const int kPassAxis[3] = {2, 1, 0};  // pass 0 = z, 1 = y, 2 = x
+croft_status build_batch_tables(const std::vector<int>& dims, const std::vector<int>& pgrid,
+                                std::vector<BatchGrid>& hgrid, std::vector<BatchItem>& items,
+                                std::vector<float>& pool, int pass_begin[4]);
 
-static croft_status build_persistent(BatchState* b) {
-    const int G = (int)b->pgrid.size();
-    if (G == 0) return CROFT_OK;
-    // twiddle pool: one table per distinct axis length
+// Host tables of the persistent schedule for the grids `pgrid` of a batch:
+// grid descriptors (pointers left NULL), the work list (pass by pass, biggest
+// grids first within a pass), the twiddle pool and the item range of each pass.
+croft_status build_batch_tables(const std::vector<int>& dims, const std::vector<int>& pgrid,
+                                std::vector<BatchGrid>& hgrid, std::vector<BatchItem>& items,
+                                std::vector<float>& pool, int pass_begin[4]) {
+    const int G = (int)pgrid.size();
     std::vector<int> lens;
-    for (int g : b->pgrid)
-        for (int a = 0; a < 3; ++a) lens.push_back(b->dims[3 * g + a]);
+    for (int g : pgrid)
+        for (int a = 0; a < 3; ++a) lens.push_back(dims[3 * g + a]);
     std::sort(lens.begin(), lens.end());
     lens.erase(std::unique(lens.begin(), lens.end()), lens.end());
-    std::vector<float> pool;
+    pool.clear();
     std::vector<int> off(CROFT_BATCH_MAX_N + 1, 0);
     for (int n : lens) {
+        if (n > CROFT_BATCH_MAX_N) return CROFT_ERR_UNSUPPORTED_SIZE;
         off[n] = (int)(pool.size() / 2);
         std::vector<float> t(2 * (size_t)n + 2, 0.f);
         if (n > 1 && host_build_twiddles(n, t.data()) != n - 1) return CROFT_ERR_UNSUPPORTED_SIZE;
         pool.insert(pool.end(), t.begin(), t.begin() + 2 * std::max(1, n - 1));
     }
-    // descriptors
-    b->hgrid.assign(G, BatchGrid{});
+    hgrid.assign(G, BatchGrid{});
     for (int i = 0; i < G; ++i) {
-        const int g = b->pgrid[i];
-        const int nx = b->dims[3 * g], ny = b->dims[3 * g + 1], nz = b->dims[3 * g + 2];
+        const int g = pgrid[i];
+        const int nx = dims[3 * g], ny = dims[3 * g + 1], nz = dims[3 * g + 2];
         const long long N = (long long)nx * ny * nz;
-        BatchGrid& D = b->hgrid[i];
+        BatchGrid& D = hgrid[i];
         D.first_pass = -1;
         int prev = -1;
         for (int p = 0; p < 3; ++p) {
             const int axis = kPassAxis[p];
-            const int n = b->dims[3 * g + axis];
+            const int n = dims[3 * g + axis];
             D.n[p] = n;
             D.M[p] = (axis == 2) ? 1 : (axis == 1 ? (long long)nz : (long long)ny * nz);
             D.ncols[p] = N / n;
@@ -136,18 +142,28 @@ static croft_status build_persistent(BatchState* b) {
             prev = p;
         }
     }
-    // work list: pass by pass; within a pass the biggest grids first
     std::vector<int> order(G);
     for (int i = 0; i < G; ++i) order[i] = i;
-    std::vector<BatchItem> items;
+    items.clear();
     for (int p = 0; p < 3; ++p) {
-        b->pass_begin[p] = (int)items.size();
-        std::sort(order.begin(), order.end(),
-                  [&](int a, int c) { return b->hgrid[a].ntiles[p] * b->hgrid[a].n[p] > b->hgrid[c].ntiles[p] * b->hgrid[c].n[p]; });
+        pass_begin[p] = (int)items.size();
+        std::sort(order.begin(), order.end(), [&](int a, int c) {
+            return (long long)hgrid[a].ntiles[p] * hgrid[a].n[p] > (long long)hgrid[c].ntiles[p] * hgrid[c].n[p];
+        });
         for (int i : order)
-            for (int t = 0; t < b->hgrid[i].ntiles[p]; ++t) items.push_back(BatchItem{i, p, t, 0});
+            for (int t = 0; t < hgrid[i].ntiles[p]; ++t) items.push_back(BatchItem{i, p, t, 0});
     }
-    b->pass_begin[3] = (int)items.size();
+    pass_begin[3] = (int)items.size();
+    return CROFT_OK;
+}
+
+static croft_status build_persistent(BatchState* b) {
+    const int G = (int)b->pgrid.size();
+    if (G == 0) return CROFT_OK;
+    std::vector<BatchItem> items;
+    std::vector<float> pool;
+    croft_status st = build_batch_tables(b->dims, b->pgrid, b->hgrid, items, pool, b->pass_begin);
+    if (st != CROFT_OK) return st;
     b->nitems = (int)items.size();
     b->scratch_ints = 8 + 3 * G;
     b->smem = batch_smem_bytes();

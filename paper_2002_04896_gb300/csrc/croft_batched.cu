@@ -133,4 +133,9 @@ int batched_blocks_per_sm(int smem) {
 
 void* batched_kernel_ptr() { return (void*)croft_batched_kernel; }
 
+cudaError_t launch_batched(const BatchArgs& A, int blocks, int smem, cudaStream_t s) {
+    croft_batched_kernel<<<blocks, CROFT_BATCH_THREADS, smem, s>>>(A);
+    return cudaGetLastError();
+}
+
 }  // namespace croft
