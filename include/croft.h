@@ -168,6 +168,55 @@ croft_status croft_plan_set_wait_limit(croft_plan plan, long long cycles);
 croft_status croft_plan_set_test_unsatisfiable_wait(croft_plan plan, int enable);
 
 /*
+ * croft_exec_batched_noalloc - the batched transform for callers that cannot
+ * allocate device memory.  The paper has no counterpart; this is a library
+ * service.
+ *
+ * Who needs it: code that runs inside a framework whose caching allocator owns
+ * all of the device's memory (so a plan's own cudaMalloc would fail or fight
+ * the pool), serving and real-time loops whose policy forbids device
+ * allocation on the request path (cudaMalloc may synchronise the device), and
+ * plug-ins that are not allowed to keep device memory of their own between
+ * calls.  Every other entry point here needs a plan, and plans allocate
+ * (twiddle tables, work lists, counters).
+ *
+ * What it does: exactly what a CROFT_BATCH_ONE_LAUNCH batched plan's exec does
+ * (same persistent kernel, same tiles, so the same bits), but the kernel's
+ * working memory - work counter, per-grid completion counts, status word, grid
+ * descriptors, work list and twiddle tables - lives in one statically sized
+ * __device__ array inside libcroft.so (about 1.1 MiB; every GPU that loads the
+ * library holds it until the process exits).  The call builds those tables on
+ * the host, copies them into the array on `stream`, clears the counters and
+ * launches; it calls no cudaMalloc / cudaFree and no allocating library
+ * routine.  The first call on a device looks up the array's device address
+ * (cudaGetSymbolAddress); make that first call before any stream capture.
+ *
+ *   count     : number of grids, 1..CROFT_NOALLOC_MAX_GRIDS.
+ *   dims      : host array of 3*count axis lengths; each axis 1..128 of the
+ *               form 2^a 3^b 5^c.
+ *   in, out   : host arrays of `count` device pointers, as for
+ *               croft_exec_batched_forward (16-byte aligned, in[g] == out[g]
+ *               or disjoint).
+ *   direction : -1 forward (Eq. 1), +1 backward (Eq. 2, unnormalised).
+ *   stream    : cudaStream_t or NULL.
+ * Returns CROFT_OK, CROFT_ERR_INVALID_ARG, CROFT_ERR_UNSUPPORTED_SIZE (more
+ * than CROFT_NOALLOC_MAX_GRIDS grids, an axis outside the list above, or more
+ * than CROFT_NOALLOC_MAX_ITEMS work items - a 128^3 grid has 1536 - i.e. the
+ * batch does not fit the static array) or CROFT_ERR_CUDA.
+ *
+ * All calls share the one array and it keeps the last call's contents, so two
+ * calls whose work overlaps on the GPU (different streams, or different host
+ * threads without ordering) race and corrupt each other; calls on one stream
+ * are ordered and safe.  The bounded device-side waits are those of the
+ * batched plans; a wait that runs out leaves the affected grids incomplete and
+ * is not reported by this call (use a batched plan when that status matters).
+ */
+#define CROFT_NOALLOC_MAX_GRIDS 256
+#define CROFT_NOALLOC_MAX_ITEMS 65536
+croft_status croft_exec_batched_noalloc(int count, const int* dims, void* const* in, void* const* out, int direction,
+                                        void* stream);
+
+/*
  * croft_exec_forward - Eq. (1), unnormalised, out = F(in).
  * croft_exec_backward - Eq. (2) with exponent +, WITHOUT the 1/N factor.
  *

@@ -24,6 +24,9 @@ CROFT_SCHEDULE_AUTO = 0
 CROFT_SCHEDULE_THREE_PASS = 1
 CROFT_SCHEDULE_PLANE_FUSED = 2
 
+CROFT_NOALLOC_MAX_GRIDS = 256
+CROFT_NOALLOC_MAX_ITEMS = 65536
+
 CROFT_BATCH_AUTO = 0
 CROFT_BATCH_ONE_LAUNCH = 1
 CROFT_BATCH_PER_PASS = 2
@@ -67,6 +70,8 @@ _exec_batched_forward = _sig("croft_exec_batched_forward", _I, [_P, ctypes.POINT
 _exec_batched_backward = _sig("croft_exec_batched_backward", _I, [_P, ctypes.POINTER(_P), ctypes.POINTER(_P), _P])
 _set_wait_limit = _sig("croft_plan_set_wait_limit", _I, [_P, ctypes.c_longlong])
 _set_test_unsat = _sig("croft_plan_set_test_unsatisfiable_wait", _I, [_P, _I])
+_exec_batched_noalloc = _sig("croft_exec_batched_noalloc", _I,
+                             [_I, ctypes.POINTER(_I), ctypes.POINTER(_P), ctypes.POINTER(_P), _I, _P])
 _twiddle_table = _sig("croft_twiddle_table", _I, [_I, ctypes.POINTER(_I), _I, ctypes.POINTER(ctypes.c_float)])
 
 LIBRARY_PATH = _LIB_PATH
@@ -76,7 +81,7 @@ EXPORTED = [
     "croft_plan_pass_times", "croft_plan_last_device_status", "croft_plan_destroy", "croft_factorize",
     "croft_twiddle_table", "croft_plan_create_batched", "croft_plan_create_batched_mode",
     "croft_exec_batched_forward", "croft_exec_batched_backward", "croft_plan_set_wait_limit",
-    "croft_plan_set_test_unsatisfiable_wait",
+    "croft_plan_set_test_unsatisfiable_wait", "croft_exec_batched_noalloc",
 ]
 
 
@@ -271,6 +276,18 @@ def croft_plan_set_wait_limit(plan: int, cycles: int) -> None:
 
 def croft_plan_set_test_unsatisfiable_wait(plan: int, enable: bool) -> None:
     _check(_set_test_unsat(plan, 1 if enable else 0), "croft_plan_set_test_unsatisfiable_wait")
+
+
+def croft_exec_batched_noalloc_status(dims, ins, outs, direction: int, stream=None) -> int:
+    """The allocation-free batched entry point: direction -1 forward (Eq. 1), +1 backward (Eq. 2)."""
+    flat = [int(v) for d in dims for v in d]
+    arr = (_I * max(1, len(flat)))(*flat)
+    return _exec_batched_noalloc(len(dims), arr, _ptr_array(ins), _ptr_array(outs), int(direction),
+                                 _stream_ptr(stream))
+
+
+def croft_exec_batched_noalloc(dims, ins, outs, direction: int, stream=None) -> None:
+    _check(croft_exec_batched_noalloc_status(dims, ins, outs, direction, stream), "croft_exec_batched_noalloc")
 
 
 class BatchPlan:
