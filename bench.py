@@ -212,6 +212,108 @@ def run_reference(args):
     return 0
 
 
+def _flush(flush):
+    flush.fill_(1.0)
+
+
+def time_transform(croft, torch, stream, flush, plan, run_fwd, run_bwd, reps=5, warm=2):
+    """Median device ms of forward and backward (L2 flushed before each) and mean per-pass ms."""
+    fw, bw, passes = [], [], []
+    for i in range(warm + reps):
+        res = []
+        for fn in (run_fwd, run_bwd):
+            with torch.cuda.stream(stream):
+                _flush(flush)
+                a = torch.cuda.Event(enable_timing=True)
+                b = torch.cuda.Event(enable_timing=True)
+                a.record(stream)
+                fn()
+                b.record(stream)
+            pt = croft.croft_plan_pass_times(plan) if plan else []
+            stream.synchronize()
+            res.append((a.elapsed_time(b), pt))
+        if i >= warm:
+            fw.append(res[0][0])
+            bw.append(res[1][0])
+            passes.append(res[0][1])
+            passes.append(res[1][1])
+    np_ = len(passes[0]) if passes and passes[0] else 0
+    pass_ms = [statistics.mean(p[i] for p in passes) for i in range(np_)]
+    return statistics.median(fw), statistics.median(bw), pass_ms
+
+
+def measure_rows(croft, torch, dev, stream, flush, peak):
+    """The other hot-path rows, timed on device-generated data (timing does not depend on values):
+    non-power-of-two meshes, FP32 vs tensor-core 512^3 (with the round-trip error of each),
+    and the 96-grid batch (one persistent launch vs per-grid plans)."""
+    import numpy as np
+
+    import synthetic_inputs as S
+
+    rows = {}
+    gen = torch.Generator(device=dev)
+    gen.manual_seed(7)
+
+    def grid(shape):
+        return torch.complex(torch.rand(shape, device=dev, generator=gen) * 2 - 1,
+                             torch.rand(shape, device=dev, generator=gen) * 2 - 1)
+
+    for name, shape, dtype in (("pme480_fp32", (480, 480, 480), 0), ("pme384x360x320_fp32", (384, 360, 320), 0),
+                               ("pme512_fp32", (512, 512, 512), 0), ("pme512_tc_bf16x3", (512, 512, 512), 1)):
+        x = grid(shape)
+        y = torch.empty_like(x)
+        z = torch.empty_like(x)
+        n = math.prod(shape)
+        with croft.Plan(*shape, dtype=dtype) as p:
+            croft.croft_plan_set_timing(p.handle, True)
+            sh = stream.cuda_stream
+            f_ms, b_ms, pass_ms = time_transform(
+                croft, torch, stream, flush, p.handle,
+                lambda: croft.croft_exec_forward(p.handle, x, y, sh),
+                lambda: croft.croft_exec_backward(p.handle, y, z, sh))
+            desc = p.describe()
+        stream.synchronize()
+        rt = float(torch.linalg.vector_norm((z - n * x).flatten()) / torch.linalg.vector_norm((n * x).flatten()))
+        t = f_ms + b_ms
+        dom = max(range(len(pass_ms)), key=lambda i: pass_ms[i])
+        rows[name] = {"shape": list(shape), "ms_fwd": f_ms, "ms_bwd": b_ms,
+                      "gflops": 2 * nominal_flops(shape) / (t * 1e-3) / 1e9,
+                      "hbm_frac_whole_transform": (32.0 * n / (t * 1e-3) / 1e9) / peak,
+                      "pass_ms": pass_ms, "dominant_pass_gbs": 16.0 * n / (pass_ms[dom] * 1e-3) / 1e9,
+                      "dominant_pass_frac": (16.0 * n / (pass_ms[dom] * 1e-3) / 1e9) / peak,
+                      "roundtrip_rel_l2": rt, "plan": desc}
+        del x, y, z
+    # the batch of 96 uneven PME meshes (seed-3 sizes), one persistent launch vs per-grid plans
+    rng = np.random.default_rng(3)
+    dims = [tuple(int(v) for v in r) for r in rng.choice(np.asarray(S.BATCH_AXIS_CHOICES), size=(96, 3))]
+    xs = [grid(d) for d in dims]
+    ys = [torch.empty_like(x) for x in xs]
+    zs = [torch.empty_like(x) for x in xs]
+    total = sum(math.prod(d) for d in dims)
+    fl = sum(2 * nominal_flops(d) for d in dims)
+    brow = {"grids": 96, "points": total, "bytes_per_grid_set": 8 * total}
+    for mode, key in ((croft.CROFT_BATCH_ONE_LAUNCH, "one_launch"), (croft.CROFT_BATCH_PER_PASS, "per_pass"),
+                      (croft.CROFT_BATCH_PER_GRID, "per_grid")):
+        with croft.BatchPlan(dims, mode=mode) as bp:
+            croft.croft_plan_set_timing(bp.handle, True)
+            sh = stream.cuda_stream
+            f_ms, b_ms, _ = time_transform(
+                croft, torch, stream, flush, bp.handle,
+                lambda: croft.croft_exec_batched_forward(bp.handle, xs, ys, sh),
+                lambda: croft.croft_exec_batched_backward(bp.handle, ys, zs, sh))
+            launches = croft.croft_plan_num_launches(bp.handle)
+        t = f_ms + b_ms
+        brow[key] = {"ms_fwd": f_ms, "ms_bwd": b_ms, "gflops": fl / (t * 1e-3) / 1e9,
+                     "hbm_frac_whole_transform": (32.0 * total / (t * 1e-3) / 1e9) / peak,
+                     "launches_per_direction": launches}
+    stream.synchronize()
+    err = max(float(torch.linalg.vector_norm((z - math.prod(d) * x).flatten()) /
+                    torch.linalg.vector_norm((math.prod(d) * x).flatten())) for d, x, z in zip(dims, xs, zs))
+    brow["roundtrip_rel_l2_max"] = err
+    rows["batch96"] = brow
+    return rows
+
+
 def run_croft(args):
     import numpy as np
     import torch
@@ -340,6 +442,10 @@ def run_croft(args):
         e2e_ms = float(t.item())
     e2e_val = world * flops_step / (e2e_ms * 1e-3) / 1e9
 
+    rows = None
+    if rank == 0 and not args.no_rows:
+        rows = measure_rows(croft, torch, dev, stream, flush, peak)
+
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         # whole forward+backward steps of the oracle, repeated for >= 10 s (at most 30 s)
@@ -374,6 +480,7 @@ def run_croft(args):
             "e2e": {"value": e2e_val, "unit": "GFLOP/s", "h2d_bytes_per_step": 8 * n_total,
                     "d2h_bytes_per_step": 8 * n_total, "ms_per_step": e2e_ms},
             "gpu_launches": launches_per_step * args.steps,
+            "rows": rows,
             "clocks": clk,
             "wall_s_timed_region": t_wall,
         }
@@ -391,6 +498,7 @@ def main():
     ap.add_argument("--impl", default="croft", choices=["croft", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--schedule", default="auto", choices=["auto", "three_pass", "plane_fused"])
+    ap.add_argument("--no-rows", action="store_true", help="skip the extra per-row measurements")
     ap.add_argument("--clock-window-s", type=float, default=2.0,
                     help="minimum wall time of the timed region, padded with untimed L2-flush writes "
                          "between steps (0 under a profiler)")

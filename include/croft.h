@@ -89,7 +89,8 @@ croft_status croft_plan_create(croft_plan* out, int nx, int ny, int nz, croft_dt
  *       crosses HBM twice.  Available for the plane shapes the library
  *       instantiates (ny x nz in {32x32, 64x64, 128x128, 256x256, 384x384});
  *       other shapes give CROFT_ERR_UNSUPPORTED_SIZE.
- *   CROFT_SCHEDULE_AUTO : PLANE_FUSED when available, else THREE_PASS.
+ *   CROFT_SCHEDULE_AUTO : THREE_PASS (measured faster on GB300 so far); with the
+ *       environment variable CROFT_SCHEDULE_AUTO_FUSED=1, PLANE_FUSED where available.
  */
 typedef enum {
     CROFT_SCHEDULE_AUTO = 0,

@@ -298,8 +298,12 @@ static croft_status create_impl(croft_plan* out, int nx, int ny, int nz, croft_d
     const int want_cluster = envc ? atoi(envc) : 0;
     const PlaneKernel* pk = (ny > 1 && nz > 1 && !want_tc) ? find_plane_kernel(ny, nz, want_cluster) : NULL;
     if (sched == CROFT_SCHEDULE_PLANE_FUSED && !pk) return fail(p, CROFT_ERR_UNSUPPORTED_SIZE);
+    // AUTO takes the fused pass only when asked to (CROFT_SCHEDULE_AUTO_FUSED=1): on GB300 the
+    // cluster exchange currently costs more than the HBM pass it saves.
+    const char* af = getenv("CROFT_SCHEDULE_AUTO_FUSED");
+    const bool auto_fused = af && af[0] == '1';
     bool fused = false;
-    if (pk && sched != CROFT_SCHEDULE_THREE_PASS) {
+    if (pk && (sched == CROFT_SCHEDULE_PLANE_FUSED || (sched == CROFT_SCHEDULE_AUTO && auto_fused))) {
         croft_status st = add_plane_pass(p, pk);
         if (st == CROFT_OK) {
             fused = true;

@@ -29,9 +29,9 @@ def dev(croft_lib):
     return torch.device("cuda:0")
 
 
-def run(croft, x_np, direction="forward", inplace=False, dtype=0):
+def run(croft, x_np, direction="forward", inplace=False, dtype=0, schedule=None):
     x = torch.from_numpy(np.ascontiguousarray(x_np)).cuda()
-    with croft.Plan(*x_np.shape, dtype=dtype) as p:
+    with croft.Plan(*x_np.shape, dtype=dtype, schedule=schedule) as p:
         out = x if inplace else torch.empty_like(x)
         getattr(p, direction)(x, out)
         torch.cuda.synchronize()
@@ -181,13 +181,13 @@ def test_fused_plane_schedule_matches_oracle(croft_lib, dev, ny, nz):
 @pytest.mark.parametrize("ny,nz", PLANE_SHAPES[:4])
 def test_fused_plane_only_no_x_axis(croft_lib, dev, ny, nz):
     x = S.white_noise((1, ny, nz), 3)
-    y = run(croft_lib, x)
+    y = run(croft_lib, x, schedule=croft_lib.CROFT_SCHEDULE_PLANE_FUSED)
     assert oracle.rel_l2(y, oracle.forward(x)) <= tol(x.shape)
 
 
-def test_schedules_agree_and_auto_prefers_fused(croft_lib, dev):
+def test_schedules_agree(croft_lib, dev):
     x = torch.from_numpy(S.white_noise((16, 256, 256), 9)).cuda()
-    with croft_lib.Plan(16, 256, 256) as pa, \
+    with croft_lib.Plan(16, 256, 256, schedule=croft_lib.CROFT_SCHEDULE_PLANE_FUSED) as pa, \
             croft_lib.Plan(16, 256, 256, schedule=croft_lib.CROFT_SCHEDULE_THREE_PASS) as p3:
         assert "yz:plane" in pa.describe()
         assert croft_lib.croft_plan_num_launches(p3.handle) == 3
