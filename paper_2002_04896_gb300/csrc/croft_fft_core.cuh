@@ -76,7 +76,7 @@ struct GlobalOutUnit {
 
 // Row-major pencil in shared memory, one pad slot per 16 elements (conflict-free
 // for the stride-R writes of the early stages).
-__host__ __device__ constexpr int row_ld(int n) { return n + (n - 1) / 16 + 1; }
+__host__ __device__ constexpr int row_ld(int n) { return croft_row_ld(n); }
 struct SmemRow {
     float2* s;  // start of this pencil
     __device__ __forceinline__ float2 load(int a) const { return s[a + (a >> 4)]; }

@@ -1,5 +1,6 @@
 // croft_internal.h - descriptors shared by the planner (host) and the pass kernels.
 #pragma once
+#include <cuda.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -35,6 +36,21 @@ struct PlaneArgs {
 };
 
 typedef void (*pass_fn)(const float2*, float2*, const PassArgs);
+
+// TMA-pipelined persistent pass (croft_pipe_kernel.cuh).
+struct PipeArgs {
+    const float2* tw;          // twiddle table (N-1 entries)
+    long long M;               // COL: element stride of the axis (inner extent of the tensor map)
+    long long ncols;           // ROW: number of pencils
+    long long ntiles;
+    long long tiles_per_row;   // COL: ceil(M / W)
+    int W;                     // pencils per tile
+    int buf_elems;             // float2 slots per buffer (>= the padded ROW layout)
+    int tw_pad;
+    int box_rows;              // COL: rows per tensor-map box (divides N, <= 256)
+    float isign;
+};
+typedef void (*pipe_fn)(const float2*, float2*, const PipeArgs, const CUtensorMap);
 typedef void (*plane_fn)(const float2*, float2*, const PlaneArgs);
 
 struct PlaneKernel {
@@ -51,6 +67,9 @@ struct PassLaunch {
     PlaneKernel pk;     // PASS_PLANE
     int layout;
     int tc;             // 1: tensor-core variant of the pass kernel
+    int pipe;           // 1: TMA-pipelined persistent variant (PipeArgs below)
+    PipeArgs pa;
+    long long B;        // pipe COL: outer extent of the tensor map (batch rows)
     int T;              // threads per pencil (fixed by the kernel: croft_threads_per_pencil)
     int grid;
     int block;
@@ -60,6 +79,10 @@ struct PassLaunch {
 // croft_planes.cu
 // fused kernel for an ny x nz plane with the given cluster size (<= 0: the default one); NULL if none
 const PlaneKernel* find_plane_kernel(int ny, int nz, int cluster);
+
+// croft_pipe.cu, two size groups: the TMA-pipelined persistent pass kernel (NULL if not instantiated)
+pipe_fn lookup_pipe_kernel_group_0(int layout, int n);
+pipe_fn lookup_pipe_kernel_group_1(int layout, int n);
 
 // croft_kernels.cu, one per size group
 pass_fn lookup_pass_kernel_group_0(int layout, int n);
@@ -73,6 +96,8 @@ void tc_dft16_matrix(unsigned char* out4096);  // B operand (hi | lo) in the ker
 
 // croft_passes.cu
 pass_fn pass_kernel_for(int layout, int n);
+pipe_fn pipe_kernel_for(int layout, int n);
+int pipe_blocks_per_sm(const PassLaunch& L);
 cudaError_t prepare_pass(const PassLaunch& L);  // once per plan: shared-memory / cluster opt-ins, occupancy check
 cudaError_t launch_pass(const PassLaunch& L, const float2* in, float2* out, cudaStream_t s);
 int active_clusters(const PassLaunch& L);  // co-resident clusters of a plane pass (0 for axis passes)

@@ -1,7 +1,62 @@
 // croft_passes.cu - finds the specialised kernel of a pass and launches it.
+#include <cudaTypedefs.h>
+
+#include <string.h>
+
+#include <mutex>
+
 #include "croft_internal.h"
 
 namespace croft {
+
+pipe_fn pipe_kernel_for(int layout, int n) {
+    pipe_fn f = lookup_pipe_kernel_group_0(layout, n);
+    if (!f) f = lookup_pipe_kernel_group_1(layout, n);
+    return f;
+}
+
+// cuTensorMapEncodeTiled through the runtime's driver entry point (no link to libcuda).
+static PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder() {
+    static std::once_flag once;
+    static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+    std::call_once(once, [] {
+        void* p = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            fn = (PFN_cuTensorMapEncodeTiled_v12000)p;
+        else
+            cudaGetLastError();
+    });
+    return fn;
+}
+
+// 3D map over the source of a COL pass: dims {M, n, B} (innermost first), box {W, box_rows, 1}.
+static bool encode_col_map(const PassLaunch& L, const float2* src, CUtensorMap* map) {
+    PFN_cuTensorMapEncodeTiled_v12000 enc = tensor_map_encoder();
+    if (!enc) return false;
+    const cuuint64_t dims[3] = {(cuuint64_t)L.pa.M, (cuuint64_t)L.args.n, (cuuint64_t)L.B};
+    const cuuint64_t strides[2] = {(cuuint64_t)L.pa.M * sizeof(float2), (cuuint64_t)L.pa.M * L.args.n * sizeof(float2)};
+    const cuuint32_t box[3] = {(cuuint32_t)L.pa.W, (cuuint32_t)L.pa.box_rows, 1};
+    const cuuint32_t estr[3] = {1, 1, 1};
+    return enc(map, CU_TENSOR_MAP_DATA_TYPE_FLOAT64, 3, (void*)src, dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+               CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
+int pipe_blocks_per_sm(const PassLaunch& L) {
+    pipe_fn f = pipe_kernel_for(L.layout, L.args.n);
+    if (!f) return 0;
+    if (L.smem > 48 * 1024 && cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, L.smem) != cudaSuccess) {
+        cudaGetLastError();
+        return 0;
+    }
+    int n = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, f, L.block, L.smem) != cudaSuccess) {
+        cudaGetLastError();
+        return 0;
+    }
+    return n;
+}
 
 pass_fn pass_kernel_for(int layout, int n) {
     pass_fn f = lookup_pass_kernel_group_0(layout, n);
@@ -42,6 +97,12 @@ cudaError_t prepare_pass(const PassLaunch& L) {
         if (e != cudaSuccess) return e;
         return nclusters > 0 ? cudaSuccess : cudaErrorInvalidConfiguration;
     }
+    if (L.pipe) {
+        pipe_fn f = pipe_kernel_for(L.layout, L.args.n);
+        if (!f || (L.layout == LAYOUT_COL && !tensor_map_encoder())) return cudaErrorInvalidValue;
+        if (L.smem <= 48 * 1024) return cudaSuccess;
+        return cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, L.smem);
+    }
     pass_fn f = L.tc ? tc_pass_kernel_for(L.layout, L.args.n) : pass_kernel_for(L.layout, L.args.n);
     if (!f) return cudaErrorInvalidValue;
     if (L.smem <= 48 * 1024) return cudaSuccess;
@@ -53,6 +114,17 @@ cudaError_t launch_pass(const PassLaunch& L, const float2* in, float2* out, cuda
         cudaLaunchAttribute attr[1];
         cudaLaunchConfig_t cfg = plane_config(L, s, attr);
         return cudaLaunchKernelEx(&cfg, L.pk.fn, in, out, L.pargs);
+    }
+    if (L.pipe) {
+        pipe_fn f = pipe_kernel_for(L.layout, L.args.n);
+        if (!f) return cudaErrorInvalidValue;
+        CUtensorMap map;
+        memset(&map, 0, sizeof(map));
+        if (L.layout == LAYOUT_COL && !encode_col_map(L, in, &map)) return cudaErrorInvalidValue;
+        PipeArgs pa = L.pa;
+        pa.isign = L.args.isign;
+        f<<<L.grid, L.block, L.smem, s>>>(in, out, pa, map);
+        return cudaGetLastError();
     }
     pass_fn f = L.tc ? tc_pass_kernel_for(L.layout, L.args.n) : pass_kernel_for(L.layout, L.args.n);
     if (!f) return cudaErrorInvalidValue;

@@ -141,6 +141,58 @@ static bool shape_pass(PassLaunch& L, int layout, int n, long long M, long long 
     return true;
 }
 
+// Launch shape of a TMA-pipelined persistent pass (croft_pipe_kernel.cuh): two tile
+// buffers per CTA, 128-byte aligned; as many resident CTAs as fit, capped by the tiles.
+static bool shape_pipe(PassLaunch& L, int layout, int n, long long M, long long ncols) {
+    memset(&L, 0, sizeof(L));
+    L.kind = PASS_AXIS;
+    L.layout = layout;
+    L.pipe = 1;
+    L.args.n = n;
+    L.args.M = M;
+    L.args.ncols = ncols;
+    const int T = croft_threads_per_pencil(n);
+    L.T = T;
+    PipeArgs& P = L.pa;
+    P.tw_pad = ((n + 15) / 16) * 16;
+    int W, buf;
+    if (layout == LAYOUT_ROW) {
+        W = (256 + T - 1) / T;
+        while (W > 1 && W * T > 512) --W;
+        buf = W * croft_row_ld(n);
+        P.ncols = ncols;
+        P.ntiles = (ncols + W - 1) / W;
+        P.M = 1;
+        L.B = 1;
+    } else {
+        W = 16;
+        while (W < 64 && 2 * W * T <= 256) W *= 2;
+        if (W * T > 512) return false;
+        buf = n * W;
+        P.M = M;
+        P.tiles_per_row = (M + W - 1) / W;
+        L.B = ncols / M;
+        P.ntiles = L.B * P.tiles_per_row;
+        int k = (n + 255) / 256;
+        while (n % k) ++k;
+        P.box_rows = n / k;
+    }
+    P.W = W;
+    P.buf_elems = ((buf + 15) / 16) * 16;
+    L.args.W = W;
+    L.block = W * T;
+    L.smem = (P.tw_pad + 2 * P.buf_elems) * (int)sizeof(float2);
+    if (L.smem > g_max_smem || L.block > 512) return false;
+    const int bps = pipe_blocks_per_sm(L);
+    if (bps < 1) return false;
+    int dev = 0, sms = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    const long long g = (long long)sms * bps;
+    L.grid = (int)(P.ntiles < g ? P.ntiles : g);
+    return L.grid > 0;
+}
+
 extern "C" {
 
 const char* croft_status_string(croft_status s) {
@@ -196,8 +248,23 @@ static croft_status add_axis_pass(croft_plan p, int axis) {
     const int n = p->dims[axis];
     // element stride of the axis; a unit stride means the pencils are contiguous rows
     const long long M = (axis == 2) ? 1 : (axis == 1 ? (long long)nz : (long long)ny * nz);
+    const int layout = M == 1 ? LAYOUT_ROW : LAYOUT_COL;
+    const char* pe = getenv("CROFT_PIPE");
+    const bool allow_pipe = !(pe && pe[0] == '0');
+    if (allow_pipe && !p->axis_tc[axis] && pipe_kernel_for(layout, n) && (layout == LAYOUT_ROW || (M % 2) == 0)) {
+        PassLaunch L;
+        if (shape_pipe(L, layout, n, M, N / n)) {
+            L.pa.tw = p->tw_dev[axis];
+            if (prepare_pass(L) == cudaSuccess) {
+                p->passes.push_back(L);
+                p->pass_axis.push_back(axis);
+                return CROFT_OK;
+            }
+            cudaGetLastError();
+        }
+    }
     PassLaunch L;
-    if (!shape_pass(L, M == 1 ? LAYOUT_ROW : LAYOUT_COL, n, M, N / n, p->axis_tc[axis])) return CROFT_ERR_UNSUPPORTED_SIZE;
+    if (!shape_pass(L, layout, n, M, N / n, p->axis_tc[axis])) return CROFT_ERR_UNSUPPORTED_SIZE;
     L.kind = PASS_AXIS;
     L.args.tw = p->tw_dev[axis];
     L.args.tc_b = p->tc_b;
@@ -360,8 +427,8 @@ int croft_plan_describe(croft_plan plan, char* buf, int cap) {
             s += tmp;
             continue;
         }
-        snprintf(tmp, sizeof(tmp), " | %s:%s%s n=%d radix=", an[plan->pass_axis[i]], L.layout == LAYOUT_ROW ? "row" : "col",
-                 L.tc ? "+tc" : "", L.args.n);
+        snprintf(tmp, sizeof(tmp), " | %s:%s%s%s n=%d radix=", an[plan->pass_axis[i]], L.layout == LAYOUT_ROW ? "row" : "col",
+                 L.tc ? "+tc" : "", L.pipe ? "+tma" : "", L.args.n);
         s += tmp;
         CroftSched sc = L.tc ? croft_make_sched_tc(L.args.n) : croft_make_sched(L.args.n);
         for (int st = 0; st < sc.count; ++st) {

@@ -73,6 +73,10 @@ CROFT_HD constexpr int croft_sched_p(const CroftSched& s, int stage) {
     return p;
 }
 
+// Padded shared-memory length of one pencil in the row layout: one pad slot per
+// 16 elements keeps the stride-R writes of the early Stockham stages conflict-free.
+CROFT_HD constexpr int croft_row_ld(int n) { return n + (n - 1) / 16 + 1; }
+
 // Per-thread element budget and threads per pencil of the pass kernels.
 CROFT_HD constexpr int croft_emax(int n) { return n <= 1024 ? 16 : 32; }
 CROFT_HD constexpr int croft_threads_per_pencil(int n) { return (n + croft_emax(n) - 1) / croft_emax(n); }
