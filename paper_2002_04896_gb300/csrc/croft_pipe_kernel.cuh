@@ -88,12 +88,53 @@ __device__ __forceinline__ void pipe_issue(const PipeArgs& A, const CUtensorMap*
     }
 }
 
+// Transform the tile held in `buf` and store it (whole CTA).  Kept out of line:
+// inlined into the tile loop, the stage code of the longer schedules overwhelmed
+// the register allocator (32 registers and heavy spilling).
+template <int LAYOUT, int N>
+__device__ __noinline__ void pipe_tile(float2* buf, float2* out, const PipeArgs& A, long long t, int c, int lane,
+                                       const float2* stw) {
+    constexpr int T = croft_threads_per_pencil(N);
+    constexpr CroftSched sc = croft_make_sched(N);
+    if (LAYOUT == LAYOUT_ROW) {
+        const long long col = t * A.W + c;
+        const bool ok = (c < A.W) && col < A.ncols;
+        const long long base = (ok ? col : 0) * N;
+        const SmemDenseIn src{buf + c * N, A.isign};
+        const SmemRow work{buf + c * row_ld(N)};
+        const GlobalOutUnit dst{out + base, A.isign};
+        if constexpr (sc.count == 1) {
+            fft_stage<N, 0, T>(src, NoBarrier{}, dst, stw, lane, ok);
+        } else {
+            fft_stage<N, 0, T>(src, CtaBarrier{}, work, stw, lane, ok);
+            __syncthreads();
+            smem_stages<N, 1, sc.count - 1, T>(work, stw, lane, ok);
+            fft_stage<N, sc.count - 1, T>(work, NoBarrier{}, dst, stw, lane, ok);
+        }
+    } else {
+        const long long b = t / A.tiles_per_row;
+        const long long m = (t - b * A.tiles_per_row) * A.W + c;
+        const bool ok = (lane < T) && m < A.M;
+        const long long base = b * (long long)N * A.M + (ok ? m : 0);
+        const SmemColIn src{buf + c, A.W, A.isign};
+        const SmemCol work{buf + c, A.W};
+        const GlobalOut dst{out + base, A.M, A.isign};
+        if constexpr (sc.count == 1) {
+            fft_stage<N, 0, T>(src, NoBarrier{}, dst, stw, lane, ok);
+        } else {
+            fft_stage<N, 0, T>(src, CtaBarrier{}, work, stw, lane, ok);
+            __syncthreads();
+            smem_stages<N, 1, sc.count - 1, T>(work, stw, lane, ok);
+            fft_stage<N, sc.count - 1, T>(work, NoBarrier{}, dst, stw, lane, ok);
+        }
+    }
+}
+
 // Shared memory: [twiddles: tw_pad float2][buffer 0][buffer 1].
 template <int LAYOUT, int N>
 __global__ void __launch_bounds__(512) croft_pipe_kernel(const float2* in, float2* out, const __grid_constant__ PipeArgs A,
                                                           const __grid_constant__ CUtensorMap tmap) {
     constexpr int T = croft_threads_per_pencil(N);
-    constexpr CroftSched sc = croft_make_sched(N);
     extern __shared__ __align__(128) float2 smem[];
     __shared__ __align__(8) uint64_t full[2];
     float2* stw = smem;
@@ -125,38 +166,7 @@ __global__ void __launch_bounds__(512) croft_pipe_kernel(const float2* in, float
         const int bsel = (int)(i & 1);
         float2* buf = bufs[bsel];
         pipe_wait(pipe_smem(&full[bsel]), (uint32_t)((i >> 1) & 1));
-        if (LAYOUT == LAYOUT_ROW) {
-            const long long col = t * A.W + c;
-            const bool ok = (c < A.W) && col < A.ncols;
-            const long long base = (ok ? col : 0) * N;
-            const SmemDenseIn src{buf + c * N, A.isign};
-            const SmemRow work{buf + c * row_ld(N)};
-            const GlobalOutUnit dst{out + base, A.isign};
-            if constexpr (sc.count == 1) {
-                fft_stage<N, 0, T>(src, NoBarrier{}, dst, stw, lane, ok);
-            } else {
-                fft_stage<N, 0, T>(src, CtaBarrier{}, work, stw, lane, ok);
-                __syncthreads();
-                smem_stages<N, 1, sc.count - 1, T>(work, stw, lane, ok);
-                fft_stage<N, sc.count - 1, T>(work, NoBarrier{}, dst, stw, lane, ok);
-            }
-        } else {
-            const long long b = t / A.tiles_per_row;
-            const long long m = (t - b * A.tiles_per_row) * A.W + c;
-            const bool ok = (lane < T) && m < A.M;
-            const long long base = b * (long long)N * A.M + (ok ? m : 0);
-            const SmemColIn src{buf + c, A.W, A.isign};
-            const SmemCol work{buf + c, A.W};
-            const GlobalOut dst{out + base, A.M, A.isign};
-            if constexpr (sc.count == 1) {
-                fft_stage<N, 0, T>(src, NoBarrier{}, dst, stw, lane, ok);
-            } else {
-                fft_stage<N, 0, T>(src, CtaBarrier{}, work, stw, lane, ok);
-                __syncthreads();
-                smem_stages<N, 1, sc.count - 1, T>(work, stw, lane, ok);
-                fft_stage<N, sc.count - 1, T>(work, NoBarrier{}, dst, stw, lane, ok);
-            }
-        }
+        pipe_tile<LAYOUT, N>(buf, out, A, t, c, lane, stw);
         __syncthreads();  // every read of this buffer done
         if (tid == 0 && i + 2 < my_tiles) {
             asm volatile("fence.proxy.async.shared::cta;" ::: "memory");

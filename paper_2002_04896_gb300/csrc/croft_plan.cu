@@ -249,8 +249,9 @@ static croft_status add_axis_pass(croft_plan p, int axis) {
     // element stride of the axis; a unit stride means the pencils are contiguous rows
     const long long M = (axis == 2) ? 1 : (axis == 1 ? (long long)nz : (long long)ny * nz);
     const int layout = M == 1 ? LAYOUT_ROW : LAYOUT_COL;
+    // the TMA-pipelined kernel is opt-in (CROFT_PIPE=1): measured slower than the plain kernel so far
     const char* pe = getenv("CROFT_PIPE");
-    const bool allow_pipe = !(pe && pe[0] == '0');
+    const bool allow_pipe = pe && pe[0] == '1';
     if (allow_pipe && !p->axis_tc[axis] && pipe_kernel_for(layout, n) && (layout == LAYOUT_ROW || (M % 2) == 0)) {
         PassLaunch L;
         if (shape_pipe(L, layout, n, M, N / n)) {
