@@ -108,7 +108,7 @@ int batch_smem_bytes() {
         const int T = croft_threads_per_pencil(N);                                                 \
         const int Wr = CROFT_BATCH_THREADS / T;                                                    \
         const int Wc = batch_col_width(N);                                                         \
-        int a = Wr * row_ld(N), b = N * Wc;                                                        \
+        int a = Wr * croft_row_ld_staged(N), b = N * Wc;                                           \
         int m = (a > b ? a : b) + tw;                                                              \
         if (m > best) best = m;                                                                    \
     }

@@ -83,8 +83,8 @@ __device__ __noinline__ void batch_tile(const BatchGrid& G, int pass, int tile, 
         const long long col = (long long)tile * W + c;
         const bool ok = c < W && col < G.ncols[pass];
         const long long base = (ok ? col : 0) * N;
-        fft_pencil<N, T>(GlobalInCG{in + base, 1, isign}, SmemRow{sbuf + (ok ? c : 0) * row_ld(N)},
-                         GlobalOutUnit{out + base, isign}, stw, lane, ok);
+        fft_pencil_row<N, T>(GlobalInCG{in + base, 1, isign}, sbuf + (ok ? c : 0) * croft_row_ld_staged(N),
+                             GlobalOutUnit{out + base, isign}, stw, lane, ok);
     } else {
         const long long M = G.M[pass];
         const int c = threadIdx.x % W;

@@ -82,6 +82,15 @@ struct SmemRow {
     __device__ __forceinline__ float2 load(int a) const { return s[a + (a >> 4)]; }
     __device__ __forceinline__ void store(int a, float2 v) const { s[a + (a >> 4)] = v; }
 };
+// Row pencil stored with the padding of one stage's output (croft_row_pad).
+template <int L, int D>
+struct SmemRowP {
+    float2* s;
+    __device__ __forceinline__ int idx(int a) const { return D == 0 ? a : a + (a / L) * D; }
+    __device__ __forceinline__ float2 load(int a) const { return s[idx(a)]; }
+    __device__ __forceinline__ void store(int a, float2 v) const { s[idx(a)] = v; }
+};
+
 // Column c of a [N][W] tile (W pencils side by side).
 struct SmemCol {
     float2* s;  // tile + c
@@ -186,6 +195,46 @@ __device__ __forceinline__ void fft_pencil(const Src& src, const Sm& work, const
         __syncthreads();
         smem_stages<N, 1, sc.count - 1, T>(work, stw, lane, ok);
         fft_stage<N, sc.count - 1, T>(work, NoBarrier{}, dst, stw, lane, ok);
+    }
+}
+
+// Padding of the buffer written by stage S of the length-N schedule.
+template <int N, int S>
+struct RowPadOf {
+    static constexpr CroftRowPad p = croft_row_pad(croft_make_sched(N), S);
+    using type = SmemRowP<p.L, p.D>;
+};
+
+// Stages [S, E) of a length-N row transform in shared memory: stage S reads the
+// layout of stage S-1's output and writes its own layout (in place, the data
+// passes through registers between the two barriers).
+template <int N, int S, int E, int T>
+__device__ __forceinline__ void row_stages(float2* base, const float2* stw, int lane, bool ok) {
+    if constexpr (S < E) {
+        const typename RowPadOf<N, S - 1>::type src{base};
+        const typename RowPadOf<N, S>::type dst{base};
+        fft_stage<N, S, T>(src, CtaBarrier{}, dst, stw, lane, ok);
+        __syncthreads();
+        row_stages<N, S + 1, E, T>(base, stw, lane, ok);
+    }
+}
+
+// A full length-N FFT of one row pencil: stage 0 src -> shared memory (pencil
+// base `base`, stride croft_row_ld_staged(N) between pencils), inner stages in
+// place, last stage -> dst.  Ends without a trailing barrier.
+template <int N, int T, class Src, class Dst>
+__device__ __forceinline__ void fft_pencil_row(const Src& src, float2* base, const Dst& dst, const float2* stw,
+                                               int lane, bool ok) {
+    constexpr CroftSched sc = croft_make_sched(N);
+    if constexpr (sc.count == 1) {
+        fft_stage<N, 0, T>(src, NoBarrier{}, dst, stw, lane, ok);
+    } else {
+        const typename RowPadOf<N, 0>::type w0{base};
+        fft_stage<N, 0, T>(src, NoBarrier{}, w0, stw, lane, ok);
+        __syncthreads();
+        row_stages<N, 1, sc.count - 1, T>(base, stw, lane, ok);
+        const typename RowPadOf<N, sc.count - 2>::type wl{base};
+        fft_stage<N, sc.count - 1, T>(wl, NoBarrier{}, dst, stw, lane, ok);
     }
 }
 

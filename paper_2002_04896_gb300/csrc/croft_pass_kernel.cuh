@@ -42,8 +42,8 @@ __global__ void __launch_bounds__(512) croft_pass_kernel(const float2* in, float
         const long long col = (long long)blockIdx.x * A.W + c;
         const bool ok = col < A.ncols;
         const long long base = col * N;
-        fft_pencil<N, T>(GlobalInUnit{in + base, A.isign}, SmemRow{sbuf + c * row_ld(N)},
-                         GlobalOutUnit{out + base, A.isign}, stw, lane, ok);
+        fft_pencil_row<N, T>(GlobalInUnit{in + base, A.isign}, sbuf + c * croft_row_ld_staged(N),
+                             GlobalOutUnit{out + base, A.isign}, stw, lane, ok);
     } else {
         const int c = threadIdx.x % A.W;
         const int lane = threadIdx.x / A.W;

@@ -115,7 +115,7 @@ static bool shape_pass(PassLaunch& L, int layout, int n, long long M, long long 
     const long long smem_cap = 100 * 1024;
     const int max_threads = 512;   // the kernels' launch bound
     if (layout == LAYOUT_ROW) {
-        const int ld = n + (n - 1) / 16 + 1;
+        const int ld = tc ? croft_row_ld(n) : croft_row_ld_staged(n);
         int W = (256 + T - 1) / T;
         if (W < 1) W = 1;
         while (W > 1 && (W * T > max_threads || (A.tw_pad + (long long)W * ld) * 8 > smem_cap)) --W;
