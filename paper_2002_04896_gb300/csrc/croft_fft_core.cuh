@@ -201,8 +201,9 @@ __device__ __forceinline__ void fft_pencil(const Src& src, const Sm& work, const
 // Padding of the buffer written by stage S of the length-N schedule.
 template <int N, int S>
 struct RowPadOf {
-    static constexpr CroftRowPad p = croft_row_pad(croft_make_sched(N), S);
-    using type = SmemRowP<p.L, p.D>;
+    static constexpr int L = croft_row_layout(N).L[S];
+    static constexpr int D = croft_row_layout(N).D[S];
+    using type = SmemRowP<L, D>;
 };
 
 // Stages [S, E) of a length-N row transform in shared memory: stage S reads the

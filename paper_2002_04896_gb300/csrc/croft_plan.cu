@@ -125,6 +125,8 @@ static bool shape_pass(PassLaunch& L, int layout, int n, long long M, long long 
     } else {
         int W = 16;
         while (W * 2 * T <= 256) W *= 2;
+        const char* cw = getenv("CROFT_COL_W");  // tuning override of the column-tile width
+        if (cw && atoi(cw) >= 1 && !tc) W = atoi(cw);
         while (W > 1 && (W * T > max_threads || (A.tw_pad + (long long)n * W) * 8 > smem_cap)) W /= 2;
         A.W = W;
         L.smem = (int)((A.tw_pad + (long long)n * W) * 8);

@@ -77,49 +77,19 @@ CROFT_HD constexpr int croft_sched_p(const CroftSched& s, int stage) {
 // 16 elements keeps the stride-R writes of the early Stockham stages conflict-free.
 CROFT_HD constexpr int croft_row_ld(int n) { return n + (n - 1) / 16 + 1; }
 
-// Per-stage padding of the row layout.  Stage s (radix R, sub-transform length P)
-// writes its outputs in runs of P consecutive elements whose starts are P*R
-// apart; with P < 16 those runs fall on the same shared-memory banks.  The
-// buffer written by stage s is therefore stored with idx(e) = e + (e / L) * D,
-// L = P*R, choosing the smallest D in [0, 16) for which the 32 elements a warp
-// writes cover the 16 bank pairs (8-byte elements) exactly twice each.
-struct CroftRowPad {
-    int L, D;
-};
-CROFT_HD constexpr CroftRowPad croft_row_pad(const CroftSched& s, int stage) {
-    int P = 1;
-    for (int i = 0; i < stage; ++i) P *= s.r[i];
-    const int L = P * s.r[stage];
-    if (P >= 16) return CroftRowPad{L, 0};
-    const int runs = (32 + P - 1) / P;
-    for (int D = 0; D < 16; ++D) {
-        int hits[16] = {0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0};
-        int lanes = 0;
-        for (int q = 0; q < runs && lanes < 32; ++q)
-            for (int i = 0; i < P && lanes < 32; ++i, ++lanes) {
-                const int e = q * L + i;
-                hits[(e + (e / L) * D) % 16] += 1;
-            }
-        bool even = true;
-        for (int b = 0; b < 16; ++b) even = even && hits[b] <= 2;
-        if (even) return CroftRowPad{L, D};
-    }
-    return CroftRowPad{L, 1};
-}
+#include "croft_row_layouts.h"
 
-// Pencil stride (float2 slots) of the per-stage padded row layout: the largest
-// padded extent over the buffers the stages write.
-CROFT_HD constexpr int croft_row_ld_staged(int n) {
-    const CroftSched s = croft_make_sched(n);
-    int ld = n;
-    for (int st = 0; st + 1 < s.count; ++st) {
-        const CroftRowPad p = croft_row_pad(s, st);
-        const int ext = (n - 1) + ((n - 1) / p.L) * p.D + 1;
-        if (ext > ld) ld = ext;
-    }
-    return ld + ((ld & 1) ? 0 : 1);  // odd stride: consecutive pencils start on different banks
-}
+// Pencil stride (float2 slots) of the row layout with per-stage padding (croft_row_layouts.h).
+CROFT_HD constexpr int croft_row_ld_staged(int n) { return croft_make_sched(n).count > 1 ? croft_row_layout(n).ld : n; }
 
 // Per-thread element budget and threads per pencil of the pass kernels.
 CROFT_HD constexpr int croft_emax(int n) { return n <= 1024 ? 16 : 32; }
-CROFT_HD constexpr int croft_threads_per_pencil(int n) { return (n + croft_emax(n) - 1) / croft_emax(n); }
+// Threads per pencil: at least n / emax, rounded up to a power of two (<= 32) or a
+// multiple of 32, so that a warp never straddles pencils unevenly.
+CROFT_HD constexpr int croft_threads_per_pencil(int n) {
+    const int t = (n + croft_emax(n) - 1) / croft_emax(n);
+    if (t > 32) return (t + 31) / 32 * 32;
+    int p = 1;
+    while (p < t) p *= 2;
+    return p;
+}
