@@ -283,6 +283,19 @@ croft_status croft_plan_destroy(croft_plan plan);
 int croft_factorize(int n, int* radices, int cap);
 int croft_twiddle_table(int n, const int* radices, int nstages, float* out);
 
+/*
+ * Testing hooks (host side only; nothing here touches the GPU).
+ *
+ * croft_debug_fail_allocation(k): the k-th device or pinned-host allocation the
+ * library makes from now on fails as if the device were out of memory (k = 0
+ * disarms).  Every entry point that allocates must then return CROFT_ERR_OOM
+ * (or fall back) and release what it had already allocated.
+ * croft_debug_live_allocations(): allocations made by the library and not yet
+ * released (a leak check).
+ */
+void croft_debug_fail_allocation(int k);
+long croft_debug_live_allocations(void);
+
 #ifdef __cplusplus
 }
 #endif

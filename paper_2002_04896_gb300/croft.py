@@ -70,6 +70,8 @@ _exec_batched_forward = _sig("croft_exec_batched_forward", _I, [_P, ctypes.POINT
 _exec_batched_backward = _sig("croft_exec_batched_backward", _I, [_P, ctypes.POINTER(_P), ctypes.POINTER(_P), _P])
 _set_wait_limit = _sig("croft_plan_set_wait_limit", _I, [_P, ctypes.c_longlong])
 _set_test_unsat = _sig("croft_plan_set_test_unsatisfiable_wait", _I, [_P, _I])
+_debug_fail_allocation = _sig("croft_debug_fail_allocation", None, [_I])
+_debug_live_allocations = _sig("croft_debug_live_allocations", ctypes.c_long, [])
 _exec_batched_noalloc = _sig("croft_exec_batched_noalloc", _I,
                              [_I, ctypes.POINTER(_I), ctypes.POINTER(_P), ctypes.POINTER(_P), _I, _P])
 _twiddle_table = _sig("croft_twiddle_table", _I, [_I, ctypes.POINTER(_I), _I, ctypes.POINTER(ctypes.c_float)])
@@ -81,7 +83,8 @@ EXPORTED = [
     "croft_plan_pass_times", "croft_plan_last_device_status", "croft_plan_destroy", "croft_factorize",
     "croft_twiddle_table", "croft_plan_create_batched", "croft_plan_create_batched_mode",
     "croft_exec_batched_forward", "croft_exec_batched_backward", "croft_plan_set_wait_limit",
-    "croft_plan_set_test_unsatisfiable_wait", "croft_exec_batched_noalloc",
+    "croft_plan_set_test_unsatisfiable_wait", "croft_exec_batched_noalloc", "croft_debug_fail_allocation",
+    "croft_debug_live_allocations",
 ]
 
 
@@ -288,6 +291,14 @@ def croft_exec_batched_noalloc_status(dims, ins, outs, direction: int, stream=No
 
 def croft_exec_batched_noalloc(dims, ins, outs, direction: int, stream=None) -> None:
     _check(croft_exec_batched_noalloc_status(dims, ins, outs, direction, stream), "croft_exec_batched_noalloc")
+
+
+def croft_debug_fail_allocation(k: int) -> None:
+    _debug_fail_allocation(int(k))
+
+
+def croft_debug_live_allocations() -> int:
+    return int(_debug_live_allocations())
 
 
 class BatchPlan:

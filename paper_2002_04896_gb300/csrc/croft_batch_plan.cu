@@ -78,11 +78,11 @@ void batch_state_destroy(BatchState* b) {
         if (b->graph[d]) cudaGraphDestroy(b->graph[d]);
     }
     if (b->staging_free) cudaEventDestroy(b->staging_free);
-    if (b->staging) cudaFreeHost(b->staging);
-    if (b->d_grids) cudaFree(b->d_grids);
-    if (b->d_items) cudaFree(b->d_items);
-    if (b->d_tw) cudaFree(b->d_tw);
-    if (b->d_scratch) cudaFree(b->d_scratch);
+    if (b->staging) host_free(b->staging);
+    dev_free(b->d_grids);
+    dev_free(b->d_items);
+    dev_free(b->d_tw);
+    dev_free(b->d_scratch);
     for (croft_plan p : b->subplans) croft_plan_destroy(p);
     delete b;
 }
@@ -176,11 +176,11 @@ static croft_status build_persistent(BatchState* b) {
     if (per_sm < 1) return CROFT_ERR_CUDA;
     b->blocks = std::max(1, std::min(sms * per_sm, b->nitems));
 
-    if (cudaMalloc((void**)&b->d_tw, sizeof(float) * std::max<size_t>(2, pool.size())) != cudaSuccess) return CROFT_ERR_OOM;
-    if (cudaMalloc((void**)&b->d_items, sizeof(BatchItem) * std::max(1, b->nitems)) != cudaSuccess) return CROFT_ERR_OOM;
-    if (cudaMalloc((void**)&b->d_grids, sizeof(BatchGrid) * G) != cudaSuccess) return CROFT_ERR_OOM;
-    if (cudaMalloc((void**)&b->d_scratch, sizeof(int) * b->scratch_ints) != cudaSuccess) return CROFT_ERR_OOM;
-    if (cudaMallocHost((void**)&b->staging, sizeof(BatchGrid) * G) != cudaSuccess) return CROFT_ERR_OOM;
+    if (dev_alloc((void**)&b->d_tw, sizeof(float) * std::max<size_t>(2, pool.size())) != cudaSuccess) return CROFT_ERR_OOM;
+    if (dev_alloc((void**)&b->d_items, sizeof(BatchItem) * std::max(1, b->nitems)) != cudaSuccess) return CROFT_ERR_OOM;
+    if (dev_alloc((void**)&b->d_grids, sizeof(BatchGrid) * G) != cudaSuccess) return CROFT_ERR_OOM;
+    if (dev_alloc((void**)&b->d_scratch, sizeof(int) * b->scratch_ints) != cudaSuccess) return CROFT_ERR_OOM;
+    if (host_alloc((void**)&b->staging, sizeof(BatchGrid) * G) != cudaSuccess) return CROFT_ERR_OOM;
     if (cudaEventCreateWithFlags(&b->staging_free, cudaEventDisableTiming) != cudaSuccess) return CROFT_ERR_CUDA;
     if (!pool.empty() && cudaMemcpy(b->d_tw, pool.data(), sizeof(float) * pool.size(), cudaMemcpyHostToDevice) != cudaSuccess)
         return CROFT_ERR_CUDA;
@@ -397,7 +397,7 @@ static croft_status autotune(croft_plan plan) {
         total += (grid_bytes(b, g) + 255) / 256 * 256;
     }
     char* buf = nullptr;
-    if (cudaMalloc((void**)&buf, total) != cudaSuccess) {
+    if (dev_alloc((void**)&buf, total) != cudaSuccess) {
         cudaGetLastError();
         return configure(b, CROFT_BATCH_ONE_LAUNCH);
     }
@@ -442,7 +442,7 @@ static croft_status autotune(croft_plan plan) {
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
     cudaStreamDestroy(s);
-    cudaFree(buf);
+    dev_free(buf);
     if (st != CROFT_OK) return st;
     tune_store(key, best_mode, b->tuned_us);
     return configure(b, best_mode);

@@ -94,6 +94,12 @@ pass_fn lookup_pass_kernel_group_3(int layout, int n);
 pass_fn tc_pass_kernel_for(int layout, int n);
 void tc_dft16_matrix(unsigned char* out4096);  // B operand (hi | lo) in the kernels' smem layout
 
+// croft_alloc.cu: all library allocations (failure injection for tests)
+cudaError_t dev_alloc(void** p, size_t bytes);
+void dev_free(void* p);
+cudaError_t host_alloc(void** p, size_t bytes);
+void host_free(void* p);
+
 // croft_passes.cu
 pass_fn pass_kernel_for(int layout, int n);
 pipe_fn pipe_kernel_for(int layout, int n);

@@ -226,12 +226,12 @@ croft_status croft_plan_destroy(croft_plan plan) {
     cudaGetDevice(&cur);
     cudaSetDevice(plan->device);
     for (int a = 0; a < 3; ++a)
-        if (plan->tw_dev[a]) cudaFree(plan->tw_dev[a]);
+        dev_free(plan->tw_dev[a]);
     for (int i = 0; i < 4; ++i)
         if (plan->ev[i]) cudaEventDestroy(plan->ev[i]);
     if (plan->batch) batch_state_destroy(plan->batch);
-    if (plan->tc_b) cudaFree(plan->tc_b);
-    if (plan->d_status) cudaFree(plan->d_status);
+    dev_free(plan->tc_b);
+    dev_free(plan->d_status);
     if (cur >= 0) cudaSetDevice(cur);
     delete plan;
     return CROFT_OK;
@@ -335,8 +335,8 @@ static croft_status create_impl(croft_plan* out, int nx, int ny, int nz, croft_d
     if (want_tc) {
         unsigned char hb[4096];
         tc_dft16_matrix(hb);
-        if (cudaMalloc((void**)&p->tc_b, 4096) != cudaSuccess) return fail(p, CROFT_ERR_OOM);
-        if (cudaMalloc((void**)&p->d_status, sizeof(int)) != cudaSuccess) return fail(p, CROFT_ERR_OOM);
+        if (dev_alloc((void**)&p->tc_b, 4096) != cudaSuccess) return fail(p, CROFT_ERR_OOM);
+        if (dev_alloc((void**)&p->d_status, sizeof(int)) != cudaSuccess) return fail(p, CROFT_ERR_OOM);
         if (cudaMemcpy(p->tc_b, hb, 4096, cudaMemcpyHostToDevice) != cudaSuccess) return fail(p, CROFT_ERR_CUDA);
         if (cudaMemset(p->d_status, 0, sizeof(int)) != cudaSuccess) return fail(p, CROFT_ERR_CUDA);
     }
@@ -357,7 +357,7 @@ static croft_status create_impl(croft_plan* out, int nx, int ny, int nz, croft_d
         if (ns < 1) return fail(p, CROFT_ERR_UNSUPPORTED_SIZE);
         std::vector<float> tw(2 * (size_t)(n - 1) + 2, 0.f);
         if (build_twiddles(n, rad, ns, tw.data()) != n - 1) return fail(p, CROFT_ERR_UNSUPPORTED_SIZE);
-        if (cudaMalloc((void**)&p->tw_dev[axis], sizeof(float2) * (size_t)n) != cudaSuccess) return fail(p, CROFT_ERR_OOM);
+        if (dev_alloc((void**)&p->tw_dev[axis], sizeof(float2) * (size_t)n) != cudaSuccess) return fail(p, CROFT_ERR_OOM);
         if (cudaMemcpy(p->tw_dev[axis], tw.data(), sizeof(float2) * (size_t)(n - 1), cudaMemcpyHostToDevice) != cudaSuccess)
             return fail(p, CROFT_ERR_CUDA);
     }
