@@ -343,7 +343,7 @@ def run_croft(args):
     flush = torch.empty(max(2 * l2, 1 << 30) // 4, dtype=torch.float32, device=dev)
 
     sched = {"auto": None, "three_pass": croft.CROFT_SCHEDULE_THREE_PASS,
-             "plane_fused": croft.CROFT_SCHEDULE_PLANE_FUSED}[args.schedule]
+             "plane_fused": croft.CROFT_SCHEDULE_PLANE_FUSED, "slab_l2": croft.CROFT_SCHEDULE_SLAB_L2}[args.schedule]
     plan = croft.Plan(*shape, schedule=sched)
     plan_desc = plan.describe()
     croft.croft_plan_set_timing(plan.handle, True)
@@ -497,7 +497,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="croft", choices=["croft", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--schedule", default="auto", choices=["auto", "three_pass", "plane_fused"])
+    ap.add_argument("--schedule", default="auto", choices=["auto", "three_pass", "plane_fused", "slab_l2"])
     ap.add_argument("--no-rows", action="store_true", help="skip the extra per-row measurements")
     ap.add_argument("--clock-window-s", type=float, default=2.0,
                     help="minimum wall time of the timed region, padded with untimed L2-flush writes "

@@ -89,13 +89,19 @@ croft_status croft_plan_create(croft_plan* out, int nx, int ny, int nz, croft_dt
  *       crosses HBM twice.  Available for the plane shapes the library
  *       instantiates (ny x nz in {32x32, 64x64, 128x128, 256x256, 384x384});
  *       other shapes give CROFT_ERR_UNSUPPORTED_SIZE.
+ *   CROFT_SCHEDULE_SLAB_L2 : steps 1-5 slab by slab: for each slab of x-planes
+ *       (about CROFT_SLAB_MB MiB, default 16) the z pass then the y pass, so the
+ *       y pass reads the z pass's output from the L2 cache and the grid crosses
+ *       HBM about twice per transform; then the x pass.  The paper's chunking of
+ *       the transposes into K pieces (Sec. 5.1), here sized to the cache.
  *   CROFT_SCHEDULE_AUTO : THREE_PASS (measured faster on GB300 so far); with the
  *       environment variable CROFT_SCHEDULE_AUTO_FUSED=1, PLANE_FUSED where available.
  */
 typedef enum {
     CROFT_SCHEDULE_AUTO = 0,
     CROFT_SCHEDULE_THREE_PASS = 1,
-    CROFT_SCHEDULE_PLANE_FUSED = 2
+    CROFT_SCHEDULE_PLANE_FUSED = 2,
+    CROFT_SCHEDULE_SLAB_L2 = 3
 } croft_schedule;
 
 /* croft_plan_create with an explicit schedule (same arguments and errors;
@@ -246,7 +252,8 @@ int croft_plan_describe(croft_plan plan, char* buf, int cap);
 
 /*
  * Per-pass timing (tracing hook).  When enabled, each exec records a CUDA
- * event on the exec stream before the first pass and after every pass.
+ * event on the exec stream before the first pass and after every logical pass
+ * (the slab schedule's z+y launches count as one pass).
  * croft_plan_pass_times waits for the last exec's events and writes the
  * duration in milliseconds of each pass into ms[0 .. min(cap, passes)-1];
  * it returns the number of passes timed, 0 when timing is off or no exec ran,

@@ -477,8 +477,8 @@ croft_status croft_plan_create_batched_mode(croft_plan* out, int count, const in
     p->dtype = dtype;
     p->device = dev;
     for (int a = 0; a < 3; ++a) p->tw_dev[a] = NULL;
-    for (int i = 0; i < 4; ++i) p->ev[i] = NULL;
     p->timing = false;
+    p->ngroups = 1;
     p->ev_count = 0;
     p->ran = false;
     p->batch = new (std::nothrow) BatchState();

@@ -62,6 +62,9 @@ enum PassKind { PASS_AXIS = 0, PASS_PLANE = 1 };
 
 struct PassLaunch {
     int kind;           // PASS_AXIS or PASS_PLANE
+    long long offset;   // element offset of this launch's sub-grid (slab schedule), 0 otherwise
+    int src_in;         // 1: reads the exec's `in` (first pass over its elements); 0: reads `out`
+    int group;          // logical pass this launch belongs to (per-pass timing)
     PassArgs args;      // PASS_AXIS
     PlaneArgs pargs;    // PASS_PLANE
     PlaneKernel pk;     // PASS_PLANE

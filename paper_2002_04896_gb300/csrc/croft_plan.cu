@@ -227,8 +227,8 @@ croft_status croft_plan_destroy(croft_plan plan) {
     cudaSetDevice(plan->device);
     for (int a = 0; a < 3; ++a)
         dev_free(plan->tw_dev[a]);
-    for (int i = 0; i < 4; ++i)
-        if (plan->ev[i]) cudaEventDestroy(plan->ev[i]);
+    for (cudaEvent_t e : plan->ev)
+        if (e) cudaEventDestroy(e);
     if (plan->batch) batch_state_destroy(plan->batch);
     dev_free(plan->tc_b);
     dev_free(plan->d_status);
@@ -244,9 +244,13 @@ static croft_status fail(croft_plan p, croft_status st) {
 }
 
 // Axis pass (z: ROW; y, x: COL) of the three-pass schedule, or the x pass of the fused one.
-static croft_status add_axis_pass(croft_plan p, int axis) {
-    const int nx = p->dims[0], ny = p->dims[1], nz = p->dims[2];
+// Axis pass over x-planes [x0, x0 + nxs) (the whole grid unless the slab schedule asks for less).
+static croft_status add_axis_pass(croft_plan p, int axis, int x0 = 0, int nxs = -1, int group = -1, int src_in = -1) {
+    const int nx = nxs < 0 ? p->dims[0] : nxs, ny = p->dims[1], nz = p->dims[2];
     const long long N = (long long)nx * ny * nz;
+    const long long offset = (long long)x0 * ny * nz;
+    const int grp = group < 0 ? p->ngroups : group;
+    const int sin = src_in < 0 ? (p->passes.empty() ? 1 : 0) : src_in;
     const int n = p->dims[axis];
     // element stride of the axis; a unit stride means the pencils are contiguous rows
     const long long M = (axis == 2) ? 1 : (axis == 1 ? (long long)nz : (long long)ny * nz);
@@ -258,9 +262,13 @@ static croft_status add_axis_pass(croft_plan p, int axis) {
         PassLaunch L;
         if (shape_pipe(L, layout, n, M, N / n)) {
             L.pa.tw = p->tw_dev[axis];
+            L.offset = offset;
+            L.src_in = sin;
+            L.group = grp;
             if (prepare_pass(L) == cudaSuccess) {
                 p->passes.push_back(L);
                 p->pass_axis.push_back(axis);
+                if (grp >= p->ngroups) p->ngroups = grp + 1;
                 return CROFT_OK;
             }
             cudaGetLastError();
@@ -272,9 +280,34 @@ static croft_status add_axis_pass(croft_plan p, int axis) {
     L.args.tw = p->tw_dev[axis];
     L.args.tc_b = p->tc_b;
     L.args.status = p->d_status;
+    L.offset = offset;
+    L.src_in = sin;
+    L.group = grp;
     if (prepare_pass(L) != cudaSuccess) return CROFT_ERR_CUDA;
     p->passes.push_back(L);
     p->pass_axis.push_back(axis);
+    if (grp >= p->ngroups) p->ngroups = grp + 1;
+    return CROFT_OK;
+}
+
+// Slab schedule: for each slab of x-planes the z pass then the y pass (the y pass
+// finds the z output in L2), all in logical pass 0; then the x pass.
+static croft_status add_slab_passes(croft_plan p, int planes) {
+    const int nx = p->dims[0], ny = p->dims[1], nz = p->dims[2];
+    for (int x0 = 0; x0 < nx; x0 += planes) {
+        const int nxs = (nx - x0 < planes) ? nx - x0 : planes;
+        bool first = true;
+        if (nz > 1) {
+            croft_status st = add_axis_pass(p, 2, x0, nxs, 0, 1);
+            if (st != CROFT_OK) return st;
+            first = false;
+        }
+        if (ny > 1) {
+            croft_status st = add_axis_pass(p, 1, x0, nxs, 0, first ? 1 : 0);
+            if (st != CROFT_OK) return st;
+        }
+    }
+    if (nx > 1) return add_axis_pass(p, 0, 0, -1, p->passes.empty() ? 0 : 1, p->passes.empty() ? 1 : 0);
     return CROFT_OK;
 }
 
@@ -290,10 +323,13 @@ static croft_status add_plane_pass(croft_plan p, const PlaneKernel* pk) {
     L.block = pk->threads;
     L.smem = pk->smem;
     L.args.n = pk->ny * pk->nz;
+    L.src_in = 1;
+    L.group = p->ngroups;
     if (L.smem > g_max_smem) return CROFT_ERR_UNSUPPORTED_SIZE;
     if (prepare_pass(L) != cudaSuccess) return CROFT_ERR_CUDA;
     p->passes.push_back(L);
     p->pass_axis.push_back(3);
+    p->ngroups += 1;
     return CROFT_OK;
 }
 
@@ -301,7 +337,8 @@ static croft_status create_impl(croft_plan* out, int nx, int ny, int nz, croft_d
     if (!out) return CROFT_ERR_INVALID_ARG;
     *out = NULL;
     if (dtype != CROFT_C2C_F32 && dtype != CROFT_C2C_F32_TC_BF16X3) return CROFT_ERR_INVALID_ARG;
-    if (sched != CROFT_SCHEDULE_AUTO && sched != CROFT_SCHEDULE_THREE_PASS && sched != CROFT_SCHEDULE_PLANE_FUSED)
+    if (sched != CROFT_SCHEDULE_AUTO && sched != CROFT_SCHEDULE_THREE_PASS && sched != CROFT_SCHEDULE_PLANE_FUSED &&
+        sched != CROFT_SCHEDULE_SLAB_L2)
         return CROFT_ERR_INVALID_ARG;
     if (!axis_supported(nx) || !axis_supported(ny) || !axis_supported(nz)) return CROFT_ERR_UNSUPPORTED_SIZE;
 
@@ -320,9 +357,9 @@ static croft_status create_impl(croft_plan* out, int nx, int ny, int nz, croft_d
     p->dtype = dtype;
     p->device = dev;
     for (int a = 0; a < 3; ++a) p->tw_dev[a] = NULL;
-    for (int i = 0; i < 4; ++i) p->ev[i] = NULL;
     p->timing = false;
     p->ev_count = 0;
+    p->ngroups = 0;
     p->ran = false;
     p->batch = NULL;
     p->tc_b = NULL;
@@ -383,6 +420,18 @@ static croft_status create_impl(croft_plan* out, int nx, int ny, int nz, croft_d
             p->pass_axis.clear();
             if (sched == CROFT_SCHEDULE_PLANE_FUSED) return fail(p, st);
         }
+    }
+    if (sched == CROFT_SCHEDULE_SLAB_L2) {
+        const char* mb = getenv("CROFT_SLAB_MB");
+        const double slab_bytes = (mb && atof(mb) > 0 ? atof(mb) : 16.0) * 1048576.0;
+        const double plane_bytes = (double)ny * nz * sizeof(float2);
+        int planes = (int)(slab_bytes / plane_bytes);
+        if (planes < 1) planes = 1;
+        if (planes > nx) planes = nx;
+        croft_status st = add_slab_passes(p, planes);
+        if (st != CROFT_OK) return fail(p, st);
+        *out = p;
+        return CROFT_OK;
     }
     const int axes_fused[1] = {0};
     const int axes_all[3] = {2, 1, 0};
@@ -463,9 +512,13 @@ int croft_plan_num_launches(croft_plan plan) {
 
 croft_status croft_plan_set_timing(croft_plan plan, int enable) {
     if (!plan) return CROFT_ERR_INVALID_ARG;
-    if (enable && !plan->ev[0]) {
-        for (int i = 0; i < 4; ++i)
-            if (cudaEventCreate(&plan->ev[i]) != cudaSuccess) { cudaGetLastError(); return CROFT_ERR_CUDA; }
+    const size_t need = (size_t)(plan->batch ? 2 : plan->ngroups + 1);
+    if (enable && plan->ev.size() < need) {
+        while (plan->ev.size() < need) {
+            cudaEvent_t e;
+            if (cudaEventCreate(&e) != cudaSuccess) { cudaGetLastError(); return CROFT_ERR_CUDA; }
+            plan->ev.push_back(e);
+        }
     }
     plan->timing = enable != 0;
     plan->ev_count = 0;
@@ -521,18 +574,21 @@ static croft_status exec_dir(croft_plan plan, const void* in, void* out, void* s
         return CROFT_ERR_CUDA;
     }
     if (tm && cudaEventRecord(plan->ev[0], s) != cudaSuccess) { cudaGetLastError(); return CROFT_ERR_CUDA; }
-    const float2* src = (const float2*)in;
-    float2* dst = (float2*)out;
     for (size_t i = 0; i < plan->passes.size(); ++i) {
         PassLaunch L = plan->passes[i];
         L.args.isign = isign;
         L.pargs.isign = isign;
+        const float2* src = (L.src_in ? (const float2*)in : (const float2*)out) + L.offset;
+        float2* dst = (float2*)out + L.offset;
         cudaError_t e = launch_pass(L, src, dst, s);
         if (e != cudaSuccess) { cudaGetLastError(); return CROFT_ERR_CUDA; }
-        if (tm && cudaEventRecord(plan->ev[i + 1], s) != cudaSuccess) { cudaGetLastError(); return CROFT_ERR_CUDA; }
-        src = dst;
+        const bool group_end = (i + 1 == plan->passes.size()) || plan->passes[i + 1].group != L.group;
+        if (tm && group_end && cudaEventRecord(plan->ev[L.group + 1], s) != cudaSuccess) {
+            cudaGetLastError();
+            return CROFT_ERR_CUDA;
+        }
     }
-    plan->ev_count = tm ? (int)plan->passes.size() + 1 : 0;
+    plan->ev_count = tm ? plan->ngroups + 1 : 0;
     plan->ran = true;
     return CROFT_OK;
 }

@@ -20,8 +20,9 @@ struct croft_plan_s {
     std::vector<int> pass_axis;       // axis index of each pass (2 = z, 1 = y, 0 = x)
     float2* tw_dev[3];                // per-axis twiddle tables (NULL for length <= 1)
     bool timing;
-    cudaEvent_t ev[4];
+    std::vector<cudaEvent_t> ev;      // one per logical pass + 1 (created when timing is enabled)
     int ev_count;                     // events recorded by the last exec
+    int ngroups;                      // logical passes (launches of one group are timed together)
     bool ran;
     croft::BatchState* batch;         // batched plans only (NULL for a single-grid plan)
     unsigned char* tc_b;              // tensor-core plans: DFT-16 operand (4 KB), else NULL
