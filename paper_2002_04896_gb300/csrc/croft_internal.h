@@ -32,6 +32,7 @@ struct PassArgs {
 struct PlaneArgs {
     const float2* tw_z;  // twiddle table of the z axis (nz-1 entries)
     const float2* tw_y;  // twiddle table of the y axis (ny-1 entries)
+    int* status;         // device status word for the bounded exchange wait, may be null
     float isign;
 };
 

@@ -319,6 +319,7 @@ static croft_status add_plane_pass(croft_plan p, const PlaneKernel* pk) {
     L.pk = *pk;
     L.pargs.tw_z = p->tw_dev[2];
     L.pargs.tw_y = p->tw_dev[1];
+    L.pargs.status = p->d_status;
     L.grid = p->dims[0] * pk->cluster;
     L.block = pk->threads;
     L.smem = pk->smem;

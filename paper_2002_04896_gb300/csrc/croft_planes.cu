@@ -1,9 +1,8 @@
 // croft_planes.cu - instantiations of the fused z+y plane kernel and their registry.
 //
-// One entry per (ny, nz) plane shape with the cluster size C chosen so that a
-// CTA's tile is ~64-140 KB and at most 1024 threads: every CTA holds NY/C rows
-// in the z phase and NZ/C columns in the y phase.  Other plane shapes run the
-// three-pass schedule.
+// Per (ny, nz) plane shape, cluster sizes C for which a CTA's two tiles (NY/C
+// padded rows for the z phase, NZ/C columns for the y phase) fit in shared
+// memory with at most 1024 threads.  Other plane shapes run the other schedules.
 #include "croft_plane_kernel.cuh"
 
 namespace croft {
@@ -14,9 +13,9 @@ namespace croft {
 
 // Several cluster sizes per shape where they fit; the first entry is the default.
 static const PlaneKernel kPlaneKernels[] = {
-    CROFT_PLANE(32, 32, 1),     CROFT_PLANE(64, 64, 1),     CROFT_PLANE(128, 128, 4),
-    CROFT_PLANE(128, 128, 2),   CROFT_PLANE(256, 256, 16),  CROFT_PLANE(256, 256, 8),
-    CROFT_PLANE(384, 384, 16),
+    CROFT_PLANE(32, 32, 1),     CROFT_PLANE(64, 64, 2),     CROFT_PLANE(64, 64, 1),
+    CROFT_PLANE(128, 128, 4),   CROFT_PLANE(128, 128, 2),   CROFT_PLANE(256, 256, 16),
+    CROFT_PLANE(256, 256, 8),   CROFT_PLANE(384, 384, 16),
 };
 
 const PlaneKernel* find_plane_kernel(int ny, int nz, int cluster) {
