@@ -121,8 +121,9 @@ croft_status croft_plan_create_schedule(croft_plan* out, int nx, int ny, int nz,
  *               one persistent kernel launch (work counter, per-grid pass
  *               dependencies as bounded device-side waits); recorded in a CUDA
  *               graph per direction.
- *           CROFT_BATCH_PER_PASS  - the same work in three persistent launches
- *               (z, y, x), ordered by kernel boundaries; CUDA graph per direction.
+ *           CROFT_BATCH_PER_PASS  - the same work in three launches (z, y, x) of
+ *               one CTA per tile, ordered by kernel boundaries; CUDA graph per
+ *               direction.
  *           CROFT_BATCH_PER_GRID  - one single-grid plan per grid, launched in turn.
  *           CROFT_BATCH_AUTO      - time the three on scratch buffers at creation
  *               and keep the fastest; the choice is cached in the text file named

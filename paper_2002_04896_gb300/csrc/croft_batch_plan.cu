@@ -3,8 +3,8 @@
 // Schedules (croft_batch_mode):
 //   ONE_LAUNCH : every tile of every pass of every grid in one persistent launch
 //                (work counter + bounded per-grid dependency waits);
-//   PER_PASS   : the same work list in three persistent launches (z, y, x);
-//                kernel boundaries order the passes, no device-side waits;
+//   PER_PASS   : the same work list in three launches (z, y, x) of one CTA per
+//                tile; kernel boundaries order the passes, no counters, no waits;
 //   PER_GRID   : one ordinary single-grid plan per grid, launched one after
 //                the other (the plain baseline).
 // ONE_LAUNCH and PER_PASS are recorded once into a CUDA graph per direction
@@ -242,11 +242,12 @@ static croft_status build_graphs(BatchState* b) {
             const int end = (nl == 1) ? b->nitems : b->pass_begin[l + 1];
             if (begin == end) continue;
             BatchArgs A = batch_args(b, l, begin, end, isign);
+            A.direct = (b->mode == CROFT_BATCH_PER_PASS) ? 1 : 0;  // per pass: one CTA per tile
             void* params[1] = {&A};
             cudaKernelNodeParams kp;
             memset(&kp, 0, sizeof(kp));
             kp.func = batched_kernel_ptr();
-            kp.gridDim = dim3((unsigned)std::min(b->blocks, end - begin), 1, 1);
+            kp.gridDim = dim3((unsigned)(A.direct ? end - begin : std::min(b->blocks, end - begin)), 1, 1);
             kp.blockDim = dim3(CROFT_BATCH_THREADS, 1, 1);
             kp.sharedMemBytes = (unsigned)b->smem;
             kp.kernelParams = params;

@@ -65,6 +65,14 @@ __global__ void __launch_bounds__(CROFT_BATCH_THREADS, 3) croft_batched_kernel(c
     extern __shared__ float2 smem[];
     __shared__ int s_item;
     __shared__ int s_ok;
+    if (A.direct) {  // kernel boundaries order the passes: nothing to count or wait for
+        const int it = A.item_begin + blockIdx.x;
+        if (it >= A.item_end) return;
+        const BatchItem w = A.items[it];
+        const BatchGrid& G = A.grids[w.grid];
+        run_tile(G, w.pass, w.tile, A.tw_pool + G.tw_off[w.pass], smem, A.isign);
+        return;
+    }
     for (;;) {
         if (threadIdx.x == 0) s_item = A.item_begin + atomicAdd(A.queue, 1);
         __syncthreads();

@@ -60,6 +60,7 @@ struct BatchArgs {
     int item_begin;       // this launch serves items [item_begin, item_end)
     int item_end;
     int extra_wait;       // test hook: grid 0's pass-1 items wait for one tile more than exists
+    int direct;           // 1: one CTA per item (item = item_begin + blockIdx.x), no counters, no waits
     float isign;
 };
 
