@@ -417,10 +417,25 @@ def run_croft(args):
     dom_key = f"pass_{axis_names[dom]}_{'x'.join(map(str, shape))}"
     traffic = ncu_traffic(dom_key)
 
-    # end to end through the C ABI with host buffers: H2D of the input, fwd, bwd, D2H of the result
+    # end to end through the C ABI with host buffers: every step uploads its input grid from
+    # pinned memory, runs forward + backward and downloads the result; the library's host
+    # pipeline overlaps the copies of one step with the transforms of its neighbours.
     x_pin = torch.from_numpy(x_h).pin_memory()
     z_pin = torch.empty_like(x_pin).pin_memory()
-    e2e = []
+    ops = croft.CROFT_OP_FORWARD | croft.CROFT_OP_BACKWARD
+    croft.croft_exec_host_pipeline(plan.handle, [x_pin] * args.warmup, [z_pin] * args.warmup, ops, stream)
+    stream.synchronize()
+    with torch.cuda.stream(stream):
+        flush.fill_(1.0)
+        a = torch.cuda.Event(enable_timing=True)
+        b = torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        croft.croft_exec_host_pipeline(plan.handle, [x_pin] * args.steps, [z_pin] * args.steps, ops, stream)
+        b.record(stream)
+    stream.synchronize()
+    e2e_ms = a.elapsed_time(b) / args.steps
+    # the same with each step's copies and transforms serialised on one stream, for reference
+    e2e_serial = []
     for i in range(args.warmup + args.steps):
         with torch.cuda.stream(stream):
             flush.fill_(1.0)
@@ -434,13 +449,15 @@ def run_croft(args):
             b.record(stream)
         stream.synchronize()
         if i >= args.warmup:
-            e2e.append(a.elapsed_time(b))
-    e2e_ms = statistics.mean(e2e)
+            e2e_serial.append(a.elapsed_time(b))
+    e2e_serial_ms = statistics.mean(e2e_serial)
     if world > 1:
         t = torch.tensor([e2e_ms], device=dev)
         torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
         e2e_ms = float(t.item())
     e2e_val = world * flops_step / (e2e_ms * 1e-3) / 1e9
+    e2e_check = float(torch.linalg.vector_norm((z_pin - n_total * x_pin).flatten()) /
+                      torch.linalg.vector_norm((n_total * x_pin).flatten()))
 
     rows = None
     if rank == 0 and not args.no_rows:
@@ -478,8 +495,14 @@ def run_croft(args):
             "hbm_frac_whole_transform": (16.0 * n_total * 2 / (ms_step * 1e-3) / 1e9) / peak,
             "cpu_baseline": cpu,
             "e2e": {"value": e2e_val, "unit": "GFLOP/s", "h2d_bytes_per_step": 8 * n_total,
-                    "d2h_bytes_per_step": 8 * n_total, "ms_per_step": e2e_ms},
+                    "d2h_bytes_per_step": 8 * n_total, "ms_per_step": e2e_ms,
+                    "api": "croft_exec_host_pipeline (upload, forward, backward, download per step; "
+                           "steps overlapped on three streams)",
+                    "roundtrip_rel_l2": e2e_check,
+                    "serialised_ms_per_step": e2e_serial_ms,
+                    "serialised_value": world * flops_step / (e2e_serial_ms * 1e-3) / 1e9},
             "gpu_launches": launches_per_step * args.steps,
+            "gpu_launches_note": "croft kernels inside the device-timed steps (the e2e region launches the same per step)",
             "rows": rows,
             "clocks": clk,
             "wall_s_timed_region": t_wall,

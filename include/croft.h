@@ -237,8 +237,34 @@ croft_status croft_exec_batched_noalloc(int count, const int* dims, void* const*
 croft_status croft_exec_forward(croft_plan plan, const void* in, void* out, void* stream);
 croft_status croft_exec_backward(croft_plan plan, const void* in, void* out, void* stream);
 
+/*
+ * croft_exec_host_pipeline - transform `count` HOST-resident grids, streaming
+ * them through the GPU.  For grid i: copy host_in[i] to the device, apply the
+ * requested operations in place (CROFT_OP_FORWARD: Eq. 1; CROFT_OP_BACKWARD:
+ * Eq. 2 unnormalised; both: forward then backward, e.g. a convolution round
+ * trip), copy the result to host_out[i].  The copies and the transform of
+ * different grids overlap: grid i+1 uploads and grid i-1 downloads while grid
+ * i is transformed, on three internal streams ordered by events (the paper's
+ * chunked overlap of communication with computation, Sec. 5.1, applied to the
+ * host link).  Stream-ordered with respect to `stream`: the pipeline starts
+ * after the work already queued on it and `stream` waits for its end.
+ *
+ *   host_in, host_out : host arrays of `count` host pointers to nx*ny*nz
+ *       complex64 each; page-locked memory (cudaMallocHost / cudaHostRegister)
+ *       for the copies to overlap.  host_in[i] == host_out[i] is allowed.
+ *   ops : CROFT_OP_FORWARD, CROFT_OP_BACKWARD or both (bitwise or).
+ * The first call allocates three device buffers of one grid each plus the
+ * streams and events; they stay with the plan (croft_plan_workspace_bytes).
+ * Single-grid plans only.  Returns CROFT_OK, CROFT_ERR_INVALID_ARG,
+ * CROFT_ERR_OOM or CROFT_ERR_CUDA.
+ */
+typedef enum { CROFT_OP_FORWARD = 1, CROFT_OP_BACKWARD = 2 } croft_op;
+croft_status croft_exec_host_pipeline(croft_plan plan, int count, const void* const* host_in, void* const* host_out,
+                                      int ops, void* stream);
+
 /* Device scratch bytes held by the plan (0 when every pass runs in place;
- * batched plans: their counters and status word). */
+ * batched plans: their counters and status word; after a host pipeline call:
+ * its three grid buffers). */
 size_t croft_plan_workspace_bytes(croft_plan plan);
 
 /* Number of kernel launches one exec of this plan issues. */

@@ -28,6 +28,9 @@ CROFT_SCHEDULE_SLAB_L2 = 3
 CROFT_NOALLOC_MAX_GRIDS = 256
 CROFT_NOALLOC_MAX_ITEMS = 65536
 
+CROFT_OP_FORWARD = 1
+CROFT_OP_BACKWARD = 2
+
 CROFT_BATCH_AUTO = 0
 CROFT_BATCH_ONE_LAUNCH = 1
 CROFT_BATCH_PER_PASS = 2
@@ -71,6 +74,8 @@ _exec_batched_forward = _sig("croft_exec_batched_forward", _I, [_P, ctypes.POINT
 _exec_batched_backward = _sig("croft_exec_batched_backward", _I, [_P, ctypes.POINTER(_P), ctypes.POINTER(_P), _P])
 _set_wait_limit = _sig("croft_plan_set_wait_limit", _I, [_P, ctypes.c_longlong])
 _set_test_unsat = _sig("croft_plan_set_test_unsatisfiable_wait", _I, [_P, _I])
+_exec_host_pipeline = _sig("croft_exec_host_pipeline", _I,
+                           [_P, _I, ctypes.POINTER(_P), ctypes.POINTER(_P), _I, _P])
 _debug_fail_allocation = _sig("croft_debug_fail_allocation", None, [_I])
 _debug_live_allocations = _sig("croft_debug_live_allocations", ctypes.c_long, [])
 _exec_batched_noalloc = _sig("croft_exec_batched_noalloc", _I,
@@ -85,7 +90,7 @@ EXPORTED = [
     "croft_twiddle_table", "croft_plan_create_batched", "croft_plan_create_batched_mode",
     "croft_exec_batched_forward", "croft_exec_batched_backward", "croft_plan_set_wait_limit",
     "croft_plan_set_test_unsatisfiable_wait", "croft_exec_batched_noalloc", "croft_debug_fail_allocation",
-    "croft_debug_live_allocations",
+    "croft_debug_live_allocations", "croft_exec_host_pipeline",
 ]
 
 
@@ -292,6 +297,29 @@ def croft_exec_batched_noalloc_status(dims, ins, outs, direction: int, stream=No
 
 def croft_exec_batched_noalloc(dims, ins, outs, direction: int, stream=None) -> None:
     _check(croft_exec_batched_noalloc_status(dims, ins, outs, direction, stream), "croft_exec_batched_noalloc")
+
+
+def _host_ptr(x) -> int:
+    if isinstance(x, int):
+        return x
+    import torch
+    if isinstance(x, torch.Tensor):
+        if x.is_cuda or x.dtype != torch.complex64 or not x.is_contiguous():
+            raise ValueError("host pipeline: expected contiguous complex64 CPU tensors (pinned for overlap)")
+        return int(x.data_ptr())
+    return int(x.ctypes.data)  # numpy array
+
+
+def croft_exec_host_pipeline_status(plan: int, host_in, host_out, ops: int, stream=None) -> int:
+    """Stream host grids through the GPU: upload, transform(s) in place, download, overlapped across grids."""
+    n = len(host_in)
+    a = (_P * max(1, n))(*[_host_ptr(x) for x in host_in])
+    b = (_P * max(1, n))(*[_host_ptr(x) for x in host_out])
+    return _exec_host_pipeline(plan, n, a, b, int(ops), _stream_ptr(stream))
+
+
+def croft_exec_host_pipeline(plan: int, host_in, host_out, ops: int, stream=None) -> None:
+    _check(croft_exec_host_pipeline_status(plan, host_in, host_out, ops, stream), "croft_exec_host_pipeline")
 
 
 def croft_debug_fail_allocation(k: int) -> None:

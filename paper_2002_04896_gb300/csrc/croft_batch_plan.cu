@@ -480,6 +480,9 @@ croft_status croft_plan_create_batched_mode(croft_plan* out, int count, const in
     for (int a = 0; a < 3; ++a) p->tw_dev[a] = NULL;
     p->timing = false;
     p->ngroups = 1;
+    p->stream = NULL;
+    p->tc_b = NULL;
+    p->d_status = NULL;
     p->ev_count = 0;
     p->ran = false;
     p->batch = new (std::nothrow) BatchState();

@@ -230,6 +230,7 @@ croft_status croft_plan_destroy(croft_plan plan) {
     for (cudaEvent_t e : plan->ev)
         if (e) cudaEventDestroy(e);
     if (plan->batch) batch_state_destroy(plan->batch);
+    if (plan->stream) stream_state_destroy(plan->stream);
     dev_free(plan->tc_b);
     dev_free(plan->d_status);
     if (cur >= 0) cudaSetDevice(cur);
@@ -363,6 +364,7 @@ static croft_status create_impl(croft_plan* out, int nx, int ny, int nz, croft_d
     p->ngroups = 0;
     p->ran = false;
     p->batch = NULL;
+    p->stream = NULL;
     p->tc_b = NULL;
     p->d_status = NULL;
     const bool want_tc = dtype == CROFT_C2C_F32_TC_BF16X3;
@@ -501,8 +503,9 @@ int croft_plan_describe(croft_plan plan, char* buf, int cap) {
 }
 
 size_t croft_plan_workspace_bytes(croft_plan plan) {
-    if (plan && plan->batch) return batch_workspace_bytes(plan);
-    return 0;
+    if (!plan) return 0;
+    if (plan->batch) return batch_workspace_bytes(plan);
+    return stream_state_bytes(plan->stream);
 }
 
 int croft_plan_num_launches(croft_plan plan) {
@@ -597,6 +600,19 @@ static croft_status exec_dir(croft_plan plan, const void* in, void* out, void* s
 croft_status croft_exec_forward(croft_plan plan, const void* in, void* out, void* stream) {
     return exec_dir(plan, in, out, stream, 1.0f);
 }
+
+}  // extern "C"
+
+namespace croft {
+croft_status exec_forward_impl(croft_plan plan, const void* in, void* out, void* stream) {
+    return exec_dir(plan, in, out, stream, 1.0f);
+}
+croft_status exec_backward_impl(croft_plan plan, const void* in, void* out, void* stream) {
+    return exec_dir(plan, in, out, stream, -1.0f);
+}
+}  // namespace croft
+
+extern "C" {
 
 croft_status croft_exec_backward(croft_plan plan, const void* in, void* out, void* stream) {
     return exec_dir(plan, in, out, stream, -1.0f);

@@ -10,6 +10,9 @@
 namespace croft {
 struct BatchState;  // croft_batch_plan.cu
 void batch_state_destroy(BatchState* b);
+struct StreamState;  // croft_stream.cu
+void stream_state_destroy(StreamState* st);
+size_t stream_state_bytes(const StreamState* st);
 }  // namespace croft
 
 struct croft_plan_s {
@@ -25,6 +28,7 @@ struct croft_plan_s {
     int ngroups;                      // logical passes (launches of one group are timed together)
     bool ran;
     croft::BatchState* batch;         // batched plans only (NULL for a single-grid plan)
+    croft::StreamState* stream;       // host-streaming executor state (created on first use)
     unsigned char* tc_b;              // tensor-core plans: DFT-16 operand (4 KB), else NULL
     int* d_status;                    // tensor-core plans: device status word, else NULL
     bool axis_tc[3];                  // axis runs the tensor-core pass kernel
