@@ -456,8 +456,9 @@ def run_croft(args):
         torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
         e2e_ms = float(t.item())
     e2e_val = world * flops_step / (e2e_ms * 1e-3) / 1e9
-    e2e_check = float(torch.linalg.vector_norm((z_pin - n_total * x_pin).flatten()) /
-                      torch.linalg.vector_norm((n_total * x_pin).flatten()))
+    zr = z_pin.numpy().astype(np.complex128)
+    xr = x_h.astype(np.complex128) * n_total
+    e2e_check = float(np.linalg.norm(zr - xr) / np.linalg.norm(xr))
 
     rows = None
     if rank == 0 and not args.no_rows:
