@@ -43,8 +43,12 @@ typedef struct croft_plan_s* croft_plan; /* opaque, owned by the library */
 
 typedef enum {
     CROFT_C2C_F32 = 0,           /* complex64 in/out, FP32 CUDA-core butterflies */
-    CROFT_C2C_F32_TC_BF16X3 = 1  /* complex64 in/out, radix-16 stages on tensor cores
+    CROFT_C2C_F32_TC_BF16X3 = 1, /* complex64 in/out, radix-16 stages on tensor cores
                                     (split bf16 hi+lo operands, FP32 accumulate) */
+    CROFT_C2C_F64 = 2            /* complex128 in/out (16-byte elements), FP64 butterflies and
+                                    twiddles: the paper's double complex (Sec. 5).  Axes: powers of
+                                    two up to 1024 and 3, 5, 6, 10, 12, 15, 48, 60, 96, 120; three-pass
+                                    schedule; single-grid plans only */
 } croft_dtype;
 
 typedef enum {
@@ -71,7 +75,7 @@ const char* croft_status_string(croft_status s);
  *   out   : receives the plan (set to NULL on failure).
  *   nx,ny,nz : axis lengths, each 1..4096 and 2^a 3^b 5^c.  A length-1 axis
  *           is the identity.
- *   dtype : CROFT_C2C_F32 or CROFT_C2C_F32_TC_BF16X3.
+ *   dtype : CROFT_C2C_F32, CROFT_C2C_F32_TC_BF16X3 or CROFT_C2C_F64.
  * Returns CROFT_OK, CROFT_ERR_INVALID_ARG (out NULL, bad dtype),
  * CROFT_ERR_UNSUPPORTED_SIZE, CROFT_ERR_OOM or CROFT_ERR_CUDA.
  * The environment variable CROFT_LOG=1 prints the chosen schedule to stderr.

@@ -19,6 +19,7 @@ _lib = ctypes.CDLL(_LIB_PATH)
 
 CROFT_C2C_F32 = 0
 CROFT_C2C_F32_TC_BF16X3 = 1
+CROFT_C2C_F64 = 2
 
 CROFT_SCHEDULE_AUTO = 0
 CROFT_SCHEDULE_THREE_PASS = 1
@@ -121,8 +122,8 @@ def _stream_ptr(stream) -> int:
     return int(stream.cuda_stream)
 
 
-def _ptr(x, numel=None) -> int:
-    """Device address of a raw pointer (int) or of a C-contiguous complex64 CUDA tensor."""
+def _ptr(x, numel=None, complex128=False) -> int:
+    """Device address of a raw pointer (int) or of a C-contiguous complex64 (complex128) CUDA tensor."""
     if x is None:
         return 0
     if isinstance(x, int):
@@ -132,8 +133,9 @@ def _ptr(x, numel=None) -> int:
         raise TypeError("expected a torch CUDA tensor or an integer device address")
     if not x.is_cuda:
         raise ValueError("croft: tensors must live on a CUDA device")
-    if x.dtype != torch.complex64:
-        raise ValueError(f"croft: expected complex64, got {x.dtype}")
+    want = torch.complex128 if complex128 else torch.complex64
+    if x.dtype != want:
+        raise ValueError(f"croft: expected {want}, got {x.dtype}")
     if not x.is_contiguous():
         raise ValueError("croft: tensors must be C-contiguous in (nx, ny, nz) order")
     if numel is not None and x.numel() != numel:
@@ -304,8 +306,8 @@ def _host_ptr(x) -> int:
         return x
     import torch
     if isinstance(x, torch.Tensor):
-        if x.is_cuda or x.dtype != torch.complex64 or not x.is_contiguous():
-            raise ValueError("host pipeline: expected contiguous complex64 CPU tensors (pinned for overlap)")
+        if x.is_cuda or x.dtype not in (torch.complex64, torch.complex128) or not x.is_contiguous():
+            raise ValueError("host pipeline: expected contiguous complex CPU tensors (pinned for overlap)")
         return int(x.data_ptr())
     return int(x.ctypes.data)  # numpy array
 
@@ -396,11 +398,12 @@ class Plan:
             self.handle = croft_plan_create_schedule(nx, ny, nz, dtype, schedule)
 
     def _out(self, inp, out):
+        f64 = self.dtype == CROFT_C2C_F64
         if out is None:
             import torch
-            out = torch.empty(self.shape, dtype=torch.complex64, device=inp.device)
+            out = torch.empty(self.shape, dtype=torch.complex128 if f64 else torch.complex64, device=inp.device)
         n = self.shape[0] * self.shape[1] * self.shape[2]
-        return _ptr(inp, n), _ptr(out, n), out
+        return _ptr(inp, n, f64), _ptr(out, n, f64), out
 
     def forward(self, inp, out=None, stream=None):
         pi, po, out = self._out(inp, out)

@@ -24,22 +24,29 @@ namespace croft {
 // operand accessors
 // ---------------------------------------------------------------------------
 
+// Accessors are templates on the complex type C (float2 or double2); the
+// float2 names below are the complex64 instances.
+
 // Pencil in HBM with element stride `stride`; conj() on the way in/out when isign = -1.
-struct GlobalIn {
-    const float2* p;
+template <class C>
+struct GlobalInT {
+    using value_type = C;
+    const C* p;
     long long stride;
     float isign;
-    __device__ __forceinline__ float2 load(int a) const {
-        float2 t = p[(long long)a * stride];
+    __device__ __forceinline__ C load(int a) const {
+        C t = p[(long long)a * stride];
         t.y *= isign;
         return t;
     }
 };
-struct GlobalInUnit {  // unit stride (contiguous pencil)
-    const float2* p;
+template <class C>
+struct GlobalInUnitT {  // unit stride (contiguous pencil)
+    using value_type = C;
+    const C* p;
     float isign;
-    __device__ __forceinline__ float2 load(int a) const {
-        float2 t = p[a];
+    __device__ __forceinline__ C load(int a) const {
+        C t = p[a];
         t.y *= isign;
         return t;
     }
@@ -47,6 +54,7 @@ struct GlobalInUnit {  // unit stride (contiguous pencil)
 // As GlobalIn, but read through L2 only (ld.global.cg): for data another CTA
 // wrote earlier in the same launch (the batched persistent kernel).
 struct GlobalInCG {
+    using value_type = float2;
     const float2* p;
     long long stride;
     float isign;
@@ -56,48 +64,60 @@ struct GlobalInCG {
         return t;
     }
 };
-struct GlobalOut {
-    float2* p;
+template <class C>
+struct GlobalOutT {
+    using value_type = C;
+    C* p;
     long long stride;
     float isign;
-    __device__ __forceinline__ void store(int a, float2 v) const {
+    __device__ __forceinline__ void store(int a, C v) const {
         v.y *= isign;
         p[(long long)a * stride] = v;
     }
 };
-struct GlobalOutUnit {
-    float2* p;
+template <class C>
+struct GlobalOutUnitT {
+    using value_type = C;
+    C* p;
     float isign;
-    __device__ __forceinline__ void store(int a, float2 v) const {
+    __device__ __forceinline__ void store(int a, C v) const {
         v.y *= isign;
         p[a] = v;
     }
 };
+using GlobalIn = GlobalInT<float2>;
+using GlobalInUnit = GlobalInUnitT<float2>;
+using GlobalOut = GlobalOutT<float2>;
+using GlobalOutUnit = GlobalOutUnitT<float2>;
 
 // Row-major pencil in shared memory, one pad slot per 16 elements (conflict-free
 // for the stride-R writes of the early stages).
 __host__ __device__ constexpr int row_ld(int n) { return croft_row_ld(n); }
 struct SmemRow {
+    using value_type = float2;
     float2* s;  // start of this pencil
     __device__ __forceinline__ float2 load(int a) const { return s[a + (a >> 4)]; }
     __device__ __forceinline__ void store(int a, float2 v) const { s[a + (a >> 4)] = v; }
 };
-// Row pencil stored with the padding of one stage's output (croft_row_pad).
-template <int L, int D>
+// Row pencil stored with the padding of one stage's output (croft_row_layouts.h).
+template <int L, int D, class C = float2>
 struct SmemRowP {
-    float2* s;
+    using value_type = C;
+    C* s;
     __device__ __forceinline__ int idx(int a) const { return D == 0 ? a : a + (a / L) * D; }
-    __device__ __forceinline__ float2 load(int a) const { return s[idx(a)]; }
-    __device__ __forceinline__ void store(int a, float2 v) const { s[idx(a)] = v; }
+    __device__ __forceinline__ C load(int a) const { return s[idx(a)]; }
+    __device__ __forceinline__ void store(int a, C v) const { s[idx(a)] = v; }
 };
-
 // Column c of a [N][W] tile (W pencils side by side).
-struct SmemCol {
-    float2* s;  // tile + c
+template <class C>
+struct SmemColT {
+    using value_type = C;
+    C* s;  // tile + c
     int W;
-    __device__ __forceinline__ float2 load(int a) const { return s[a * W]; }
-    __device__ __forceinline__ void store(int a, float2 v) const { s[a * W] = v; }
+    __device__ __forceinline__ C load(int a) const { return s[a * W]; }
+    __device__ __forceinline__ void store(int a, C v) const { s[a * W] = v; }
 };
+using SmemCol = SmemColT<float2>;
 
 // ---------------------------------------------------------------------------
 // barriers
@@ -127,15 +147,16 @@ struct Tc16Sched {
 // the stage
 // ---------------------------------------------------------------------------
 template <class SchedT, int S, int T, class Src, class Mid, class Dst>
-__device__ __forceinline__ void fft_stage_s(const Src& src, const Mid& mid, const Dst& dst, const float2* stw,
-                                            int lane, bool ok) {
+__device__ __forceinline__ void fft_stage_s(const Src& src, const Mid& mid, const Dst& dst,
+                                            const typename Src::value_type* stw, int lane, bool ok) {
+    using C = typename Src::value_type;
     constexpr int N = SchedT::N;
     constexpr CroftSched sc = SchedT::get();
     constexpr int R = sc.r[S];
     constexpr int P = croft_sched_p(sc, S);
     constexpr int NB = N / R;
     constexpr int QM = (NB + T - 1) / T;
-    float2 v[QM][R];
+    C v[QM][R];
 #pragma unroll
     for (int q = 0; q < QM; ++q) {
         const int b = lane + q * T;
@@ -151,7 +172,7 @@ __device__ __forceinline__ void fft_stage_s(const Src& src, const Mid& mid, cons
         if (ok && (NB % T == 0 || b < NB)) {
             const int k = (P == 1) ? 0 : b % P;
             if (P > 1) {
-                const float2* w = stw + (P - 1) + k;
+                const C* w = stw + (P - 1) + k;
 #pragma unroll
                 for (int j = 1; j < R; ++j) v[q][j] = cmul(v[q][j], w[(j - 1) * P]);
             }
@@ -164,15 +185,15 @@ __device__ __forceinline__ void fft_stage_s(const Src& src, const Mid& mid, cons
 }
 
 template <int N, int S, int T, class Src, class Mid, class Dst>
-__device__ __forceinline__ void fft_stage(const Src& src, const Mid& mid, const Dst& dst, const float2* stw, int lane,
-                                          bool ok) {
+__device__ __forceinline__ void fft_stage(const Src& src, const Mid& mid, const Dst& dst,
+                                          const typename Src::value_type* stw, int lane, bool ok) {
     fft_stage_s<DefaultSched<N>, S, T>(src, mid, dst, stw, lane, ok);
 }
 
 // Stages [S, E) of a length-N FFT entirely in shared memory (in place), each
 // followed by a CTA barrier.  `Sm` is SmemRow or SmemCol.
 template <int N, int S, int E, int T, class Sm>
-__device__ __forceinline__ void smem_stages(const Sm& sm, const float2* stw, int lane, bool ok) {
+__device__ __forceinline__ void smem_stages(const Sm& sm, const typename Sm::value_type* stw, int lane, bool ok) {
     if constexpr (S < E) {
         fft_stage<N, S, T>(sm, CtaBarrier{}, sm, stw, lane, ok);
         __syncthreads();
@@ -185,8 +206,8 @@ __device__ __forceinline__ void smem_stages(const Sm& sm, const float2* stw, int
 // single-stage schedule src -> dst directly.  `work` must not alias src/dst.
 // Ends without a trailing barrier when dst is not shared memory.
 template <int N, int T, class Src, class Sm, class Dst>
-__device__ __forceinline__ void fft_pencil(const Src& src, const Sm& work, const Dst& dst, const float2* stw,
-                                           int lane, bool ok) {
+__device__ __forceinline__ void fft_pencil(const Src& src, const Sm& work, const Dst& dst,
+                                           const typename Src::value_type* stw, int lane, bool ok) {
     constexpr CroftSched sc = croft_make_sched(N);
     if constexpr (sc.count == 1) {
         fft_stage<N, 0, T>(src, NoBarrier{}, dst, stw, lane, ok);
@@ -199,21 +220,21 @@ __device__ __forceinline__ void fft_pencil(const Src& src, const Sm& work, const
 }
 
 // Padding of the buffer written by stage S of the length-N schedule.
-template <int N, int S>
+template <int N, int S, class C = float2>
 struct RowPadOf {
     static constexpr int L = croft_row_layout(N).L[S];
     static constexpr int D = croft_row_layout(N).D[S];
-    using type = SmemRowP<L, D>;
+    using type = SmemRowP<L, D, C>;
 };
 
 // Stages [S, E) of a length-N row transform in shared memory: stage S reads the
 // layout of stage S-1's output and writes its own layout (in place, the data
 // passes through registers between the two barriers).
-template <int N, int S, int E, int T>
-__device__ __forceinline__ void row_stages(float2* base, const float2* stw, int lane, bool ok) {
+template <int N, int S, int E, int T, class C>
+__device__ __forceinline__ void row_stages(C* base, const C* stw, int lane, bool ok) {
     if constexpr (S < E) {
-        const typename RowPadOf<N, S - 1>::type src{base};
-        const typename RowPadOf<N, S>::type dst{base};
+        const typename RowPadOf<N, S - 1, C>::type src{base};
+        const typename RowPadOf<N, S, C>::type dst{base};
         fft_stage<N, S, T>(src, CtaBarrier{}, dst, stw, lane, ok);
         __syncthreads();
         row_stages<N, S + 1, E, T>(base, stw, lane, ok);
@@ -224,17 +245,18 @@ __device__ __forceinline__ void row_stages(float2* base, const float2* stw, int 
 // base `base`, stride croft_row_ld_staged(N) between pencils), inner stages in
 // place, last stage -> dst.  Ends without a trailing barrier.
 template <int N, int T, class Src, class Dst>
-__device__ __forceinline__ void fft_pencil_row(const Src& src, float2* base, const Dst& dst, const float2* stw,
-                                               int lane, bool ok) {
+__device__ __forceinline__ void fft_pencil_row(const Src& src, typename Src::value_type* base, const Dst& dst,
+                                               const typename Src::value_type* stw, int lane, bool ok) {
+    using C = typename Src::value_type;
     constexpr CroftSched sc = croft_make_sched(N);
     if constexpr (sc.count == 1) {
         fft_stage<N, 0, T>(src, NoBarrier{}, dst, stw, lane, ok);
     } else {
-        const typename RowPadOf<N, 0>::type w0{base};
+        const typename RowPadOf<N, 0, C>::type w0{base};
         fft_stage<N, 0, T>(src, NoBarrier{}, w0, stw, lane, ok);
         __syncthreads();
         row_stages<N, 1, sc.count - 1, T>(base, stw, lane, ok);
-        const typename RowPadOf<N, sc.count - 2>::type wl{base};
+        const typename RowPadOf<N, sc.count - 2, C>::type wl{base};
         fft_stage<N, sc.count - 1, T>(wl, NoBarrier{}, dst, stw, lane, ok);
     }
 }

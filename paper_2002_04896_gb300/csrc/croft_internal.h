@@ -24,6 +24,7 @@ struct PassArgs {
     int W;              // pencils per CTA
     int tw_pad;         // float2 slots reserved for twiddles in shared memory
     float isign;        // +1 forward, -1 backward (conj-in / conj-out)
+    const double2* tw64;        // complex128 passes: the twiddle table in double precision
     const unsigned char* tc_b;  // tensor-core passes: 16-point DFT matrix, bf16 hi | lo, core-matrix layout (4 KB)
     int* status;                // tensor-core passes: device status word (bounded waits), may be null
 };
@@ -37,6 +38,7 @@ struct PlaneArgs {
 };
 
 typedef void (*pass_fn)(const float2*, float2*, const PassArgs);
+typedef void (*pass64_fn)(const double2*, double2*, const PassArgs);
 
 // TMA-pipelined persistent pass (croft_pipe_kernel.cuh).
 struct PipeArgs {
@@ -71,6 +73,7 @@ struct PassLaunch {
     PlaneKernel pk;     // PASS_PLANE
     int layout;
     int tc;             // 1: tensor-core variant of the pass kernel
+    int f64;            // 1: complex128 pass kernel
     int pipe;           // 1: TMA-pipelined persistent variant (PipeArgs below)
     PipeArgs pa;
     long long B;        // pipe COL: outer extent of the tensor map (batch rows)
@@ -104,12 +107,15 @@ void dev_free(void* p);
 cudaError_t host_alloc(void** p, size_t bytes);
 void host_free(void* p);
 
+// croft_kernels64.cu: complex128 pass kernels (NULL when n has no instantiation)
+pass64_fn pass64_kernel_for(int layout, int n);
+
 // croft_passes.cu
 pass_fn pass_kernel_for(int layout, int n);
 pipe_fn pipe_kernel_for(int layout, int n);
 int pipe_blocks_per_sm(const PassLaunch& L);
 cudaError_t prepare_pass(const PassLaunch& L);  // once per plan: shared-memory / cluster opt-ins, occupancy check
-cudaError_t launch_pass(const PassLaunch& L, const float2* in, float2* out, cudaStream_t s);
+cudaError_t launch_pass(const PassLaunch& L, const void* in, void* out, cudaStream_t s);
 int active_clusters(const PassLaunch& L);  // co-resident clusters of a plane pass (0 for axis passes)
 
 }  // namespace croft

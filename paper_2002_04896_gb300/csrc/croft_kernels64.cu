@@ -1,0 +1,28 @@
+// croft_kernels64.cu - complex128 instantiations of the pass kernel.
+//
+// Double precision is the paper's own precision (Sec. 5: double complex data).
+// On GB300 the FP64 units are a small fraction of the FP32 ones, so these
+// passes are arithmetic-bound rather than HBM-bound; they exist for the
+// paper's accuracy and for a like-for-like comparison with its FFTW3-based
+// double-complex runs, not as a fast path.  Lengths: every power of two up to
+// 1024 and a few mixed-radix ones.
+#include "croft_pass_kernel.cuh"
+
+namespace croft {
+
+#define CROFT_SIZES64(X) \
+    X(2) X(3) X(4) X(5) X(6) X(8) X(10) X(12) X(15) X(16) X(32) X(48) X(60) X(64) X(96) X(120) X(128) X(256) X(512) X(1024)
+
+pass64_fn pass64_kernel_for(int layout, int n) {
+#define CROFT_CASE64(N)                                                                 \
+    case N:                                                                             \
+        return layout == LAYOUT_ROW ? croft_pass_kernel<LAYOUT_ROW, N, double2>         \
+                                    : croft_pass_kernel<LAYOUT_COL, N, double2>;
+    switch (n) {
+        CROFT_SIZES64(CROFT_CASE64)
+        default: return nullptr;
+    }
+#undef CROFT_CASE64
+}
+
+}  // namespace croft

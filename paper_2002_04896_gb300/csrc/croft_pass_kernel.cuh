@@ -25,16 +25,20 @@
 
 namespace croft {
 
-// Shared memory: [twiddles: tw_pad float2][tile: W pencils].
-template <int LAYOUT, int N>
-__global__ void __launch_bounds__(512) croft_pass_kernel(const float2* in, float2* out,
-                                                          const __grid_constant__ PassArgs A) {
+// Shared memory: [twiddles: tw_pad elements][tile: W pencils].  C = float2
+// (complex64, the default) or double2 (complex128, twiddles from A.tw64).
+template <int LAYOUT, int N, class C = float2>
+__global__ void __launch_bounds__(512) croft_pass_kernel(const C* in, C* out, const __grid_constant__ PassArgs A) {
     constexpr int T = croft_threads_per_pencil(N);
-    extern __shared__ float2 smem[];
-    float2* stw = smem;
-    float2* sbuf = smem + A.tw_pad;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    C* smem = reinterpret_cast<C*>(smem_raw);
+    C* stw = smem;
+    C* sbuf = smem + A.tw_pad;
+    const C* twg;
+    if constexpr (sizeof(C) == 16) twg = A.tw64;
+    else twg = A.tw;
     if (croft_make_sched(N).count > 1)
-        for (int i = threadIdx.x; i < N - 1; i += blockDim.x) stw[i] = A.tw[i];
+        for (int i = threadIdx.x; i < N - 1; i += blockDim.x) stw[i] = twg[i];
 
     if (LAYOUT == LAYOUT_ROW) {
         const int c = threadIdx.x / T;
@@ -42,8 +46,8 @@ __global__ void __launch_bounds__(512) croft_pass_kernel(const float2* in, float
         const long long col = (long long)blockIdx.x * A.W + c;
         const bool ok = col < A.ncols;
         const long long base = col * N;
-        fft_pencil_row<N, T>(GlobalInUnit{in + base, A.isign}, sbuf + c * croft_row_ld_staged(N),
-                             GlobalOutUnit{out + base, A.isign}, stw, lane, ok);
+        fft_pencil_row<N, T>(GlobalInUnitT<C>{in + base, A.isign}, sbuf + c * croft_row_ld_staged(N),
+                             GlobalOutUnitT<C>{out + base, A.isign}, stw, lane, ok);
     } else {
         const int c = threadIdx.x % A.W;
         const int lane = threadIdx.x / A.W;
@@ -52,8 +56,8 @@ __global__ void __launch_bounds__(512) croft_pass_kernel(const float2* in, float
         const long long b = col / A.M;
         const long long m = col - b * A.M;
         const long long base = b * (long long)N * A.M + m;
-        fft_pencil<N, T>(GlobalIn{in + base, A.M, A.isign}, SmemCol{sbuf + c, A.W},
-                         GlobalOut{out + base, A.M, A.isign}, stw, lane, ok);
+        fft_pencil<N, T>(GlobalInT<C>{in + base, A.M, A.isign}, SmemColT<C>{sbuf + c, A.W},
+                         GlobalOutT<C>{out + base, A.M, A.isign}, stw, lane, ok);
     }
 }
 

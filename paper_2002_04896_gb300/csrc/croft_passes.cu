@@ -103,13 +103,27 @@ cudaError_t prepare_pass(const PassLaunch& L) {
         if (L.smem <= 48 * 1024) return cudaSuccess;
         return cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, L.smem);
     }
+    if (L.f64) {
+        pass64_fn f = pass64_kernel_for(L.layout, L.args.n);
+        if (!f) return cudaErrorInvalidValue;
+        if (L.smem <= 48 * 1024) return cudaSuccess;
+        return cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, L.smem);
+    }
     pass_fn f = L.tc ? tc_pass_kernel_for(L.layout, L.args.n) : pass_kernel_for(L.layout, L.args.n);
     if (!f) return cudaErrorInvalidValue;
     if (L.smem <= 48 * 1024) return cudaSuccess;
     return cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, L.smem);
 }
 
-cudaError_t launch_pass(const PassLaunch& L, const float2* in, float2* out, cudaStream_t s) {
+cudaError_t launch_pass(const PassLaunch& L, const void* vin, void* vout, cudaStream_t s) {
+    if (L.f64) {
+        pass64_fn f = pass64_kernel_for(L.layout, L.args.n);
+        if (!f) return cudaErrorInvalidValue;
+        f<<<L.grid, L.block, L.smem, s>>>((const double2*)vin, (double2*)vout, L.args);
+        return cudaGetLastError();
+    }
+    const float2* in = (const float2*)vin;
+    float2* out = (float2*)vout;
     if (L.kind == PASS_PLANE) {
         cudaLaunchAttribute attr[1];
         cudaLaunchConfig_t cfg = plane_config(L, s, attr);

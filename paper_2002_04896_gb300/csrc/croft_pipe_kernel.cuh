@@ -26,6 +26,7 @@ namespace croft {
 
 // Dense pencil c of a ROW tile as written by the bulk copy; conj on read when isign = -1.
 struct SmemDenseIn {
+    using value_type = float2;
     const float2* s;
     float isign;
     __device__ __forceinline__ float2 load(int a) const {
@@ -35,6 +36,7 @@ struct SmemDenseIn {
     }
 };
 struct SmemColIn {
+    using value_type = float2;
     const float2* s;
     int W;
     float isign;

@@ -61,6 +61,25 @@ static void twiddle64(long long r, long long N, double* re, double* im) {
     *im = y;
 }
 
+// The same table in double precision (complex128 plans).
+static int build_twiddles64(int n, const int* radices, int ns, double* out) {
+    int p = 1;
+    for (int s = 0; s < ns; ++s) {
+        int R = radices[s];
+        if (R < 2 || p * R > n) return -1;
+        for (int j = 1; j < R; ++j)
+            for (int k = 0; k < p; ++k) {
+                double re, im;
+                twiddle64((long long)j * k, (long long)p * R, &re, &im);
+                long long idx = (long long)(p - 1) + (long long)(j - 1) * p + k;
+                out[2 * idx] = re;
+                out[2 * idx + 1] = im;
+            }
+        p *= R;
+    }
+    return p == n ? n - 1 : -1;
+}
+
 static int build_twiddles(int n, const int* radices, int ns, float* out) {
     int p = 1;
     for (int s = 0; s < ns; ++s) {
@@ -101,10 +120,13 @@ static int g_max_smem = 0;
 // COL: W adjacent columns per CTA, W a multiple of 16 (128-byte rows).
 // Aim for ~256 threads per CTA and <= 100 KB of shared memory so that at
 // least two CTAs share an SM.
-static bool shape_pass(PassLaunch& L, int layout, int n, long long M, long long ncols, bool tc = false) {
+static bool shape_pass(PassLaunch& L, int layout, int n, long long M, long long ncols, bool tc = false,
+                       bool f64 = false) {
     memset(&L, 0, sizeof(L));
     L.layout = layout;
     L.tc = tc ? 1 : 0;
+    L.f64 = f64 ? 1 : 0;
+    const long long es = f64 ? 16 : 8;  // bytes per element
     PassArgs& A = L.args;
     A.n = n;
     A.M = M;
@@ -118,18 +140,18 @@ static bool shape_pass(PassLaunch& L, int layout, int n, long long M, long long 
         const int ld = tc ? croft_row_ld(n) : croft_row_ld_staged(n);
         int W = (256 + T - 1) / T;
         if (W < 1) W = 1;
-        while (W > 1 && (W * T > max_threads || (A.tw_pad + (long long)W * ld) * 8 > smem_cap)) --W;
+        while (W > 1 && (W * T > max_threads || (A.tw_pad + (long long)W * ld) * es > smem_cap)) --W;
         if ((long long)W > ncols && !tc) W = (int)ncols;  // (tensor-core tiles keep whole 128-row groups)
         A.W = W;
-        L.smem = (int)((A.tw_pad + (long long)W * ld) * 8);
+        L.smem = (int)((A.tw_pad + (long long)W * ld) * es);
     } else {
         int W = 16;
         while (W * 2 * T <= 256) W *= 2;
         const char* cw = getenv("CROFT_COL_W");  // tuning override of the column-tile width
         if (cw && atoi(cw) >= 1 && !tc) W = atoi(cw);
-        while (W > 1 && (W * T > max_threads || (A.tw_pad + (long long)n * W) * 8 > smem_cap)) W /= 2;
+        while (W > 1 && (W * T > max_threads || (A.tw_pad + (long long)n * W) * es > smem_cap)) W /= 2;
         A.W = W;
-        L.smem = (int)((A.tw_pad + (long long)n * W) * 8);
+        L.smem = (int)((A.tw_pad + (long long)n * W) * es);
     }
     if (croft_make_sched(n).count <= 1 && !tc) L.smem = 0;  // single-stage kernels touch no shared memory
     if (tc) L.smem += 4096;                                  // + the DFT-16 operand
@@ -259,7 +281,8 @@ static croft_status add_axis_pass(croft_plan p, int axis, int x0 = 0, int nxs = 
     // the TMA-pipelined kernel is opt-in (CROFT_PIPE=1): measured slower than the plain kernel so far
     const char* pe = getenv("CROFT_PIPE");
     const bool allow_pipe = pe && pe[0] == '1';
-    if (allow_pipe && !p->axis_tc[axis] && pipe_kernel_for(layout, n) && (layout == LAYOUT_ROW || (M % 2) == 0)) {
+    const bool f64 = p->dtype == CROFT_C2C_F64;
+    if (allow_pipe && !f64 && !p->axis_tc[axis] && pipe_kernel_for(layout, n) && (layout == LAYOUT_ROW || (M % 2) == 0)) {
         PassLaunch L;
         if (shape_pipe(L, layout, n, M, N / n)) {
             L.pa.tw = p->tw_dev[axis];
@@ -276,9 +299,10 @@ static croft_status add_axis_pass(croft_plan p, int axis, int x0 = 0, int nxs = 
         }
     }
     PassLaunch L;
-    if (!shape_pass(L, layout, n, M, N / n, p->axis_tc[axis])) return CROFT_ERR_UNSUPPORTED_SIZE;
+    if (!shape_pass(L, layout, n, M, N / n, p->axis_tc[axis], f64)) return CROFT_ERR_UNSUPPORTED_SIZE;
     L.kind = PASS_AXIS;
     L.args.tw = p->tw_dev[axis];
+    L.args.tw64 = f64 ? (const double2*)p->tw_dev[axis] : nullptr;
     L.args.tc_b = p->tc_b;
     L.args.status = p->d_status;
     L.offset = offset;
@@ -338,7 +362,13 @@ static croft_status add_plane_pass(croft_plan p, const PlaneKernel* pk) {
 static croft_status create_impl(croft_plan* out, int nx, int ny, int nz, croft_dtype dtype, croft_schedule sched) {
     if (!out) return CROFT_ERR_INVALID_ARG;
     *out = NULL;
-    if (dtype != CROFT_C2C_F32 && dtype != CROFT_C2C_F32_TC_BF16X3) return CROFT_ERR_INVALID_ARG;
+    if (dtype != CROFT_C2C_F32 && dtype != CROFT_C2C_F32_TC_BF16X3 && dtype != CROFT_C2C_F64) return CROFT_ERR_INVALID_ARG;
+    if (dtype == CROFT_C2C_F64) {
+        // complex128: three-pass schedule on the instantiated lengths only
+        if (sched == CROFT_SCHEDULE_PLANE_FUSED || sched == CROFT_SCHEDULE_SLAB_L2) return CROFT_ERR_UNSUPPORTED_SIZE;
+        for (int v : {nx, ny, nz})
+            if (v > 1 && !pass64_kernel_for(LAYOUT_ROW, v)) return CROFT_ERR_UNSUPPORTED_SIZE;
+    }
     if (sched != CROFT_SCHEDULE_AUTO && sched != CROFT_SCHEDULE_THREE_PASS && sched != CROFT_SCHEDULE_PLANE_FUSED &&
         sched != CROFT_SCHEDULE_SLAB_L2)
         return CROFT_ERR_INVALID_ARG;
@@ -395,6 +425,14 @@ static croft_status create_impl(croft_plan* out, int nx, int ny, int nz, croft_d
             ns = factorize(n, rad, CROFT_MAX_STAGES);
         }
         if (ns < 1) return fail(p, CROFT_ERR_UNSUPPORTED_SIZE);
+        if (dtype == CROFT_C2C_F64) {
+            std::vector<double> tw(2 * (size_t)(n - 1) + 2, 0.0);
+            if (build_twiddles64(n, rad, ns, tw.data()) != n - 1) return fail(p, CROFT_ERR_UNSUPPORTED_SIZE);
+            if (dev_alloc((void**)&p->tw_dev[axis], sizeof(double2) * (size_t)n) != cudaSuccess) return fail(p, CROFT_ERR_OOM);
+            if (cudaMemcpy(p->tw_dev[axis], tw.data(), sizeof(double2) * (size_t)(n - 1), cudaMemcpyHostToDevice) != cudaSuccess)
+                return fail(p, CROFT_ERR_CUDA);
+            continue;
+        }
         std::vector<float> tw(2 * (size_t)(n - 1) + 2, 0.f);
         if (build_twiddles(n, rad, ns, tw.data()) != n - 1) return fail(p, CROFT_ERR_UNSUPPORTED_SIZE);
         if (dev_alloc((void**)&p->tw_dev[axis], sizeof(float2) * (size_t)n) != cudaSuccess) return fail(p, CROFT_ERR_OOM);
@@ -406,7 +444,7 @@ static croft_status create_impl(croft_plan* out, int nx, int ny, int nz, croft_d
     // and its cluster fits on this device, else one pass per axis (z, y, x)
     const char* envc = getenv("CROFT_PLANE_CLUSTER");
     const int want_cluster = envc ? atoi(envc) : 0;
-    const PlaneKernel* pk = (ny > 1 && nz > 1 && !want_tc) ? find_plane_kernel(ny, nz, want_cluster) : NULL;
+    const PlaneKernel* pk = (ny > 1 && nz > 1 && !want_tc && dtype != CROFT_C2C_F64) ? find_plane_kernel(ny, nz, want_cluster) : NULL;
     if (sched == CROFT_SCHEDULE_PLANE_FUSED && !pk) return fail(p, CROFT_ERR_UNSUPPORTED_SIZE);
     // AUTO takes the fused pass only when asked to (CROFT_SCHEDULE_AUTO_FUSED=1): on GB300 the
     // cluster exchange currently costs more than the HBM pass it saves.
@@ -559,7 +597,7 @@ static croft_status exec_dir(croft_plan plan, const void* in, void* out, void* s
     if (!plan || !in || !out || plan->batch) return CROFT_ERR_INVALID_ARG;
     if (((uintptr_t)in & 15) || ((uintptr_t)out & 15)) return CROFT_ERR_INVALID_ARG;
     const long long N = (long long)plan->dims[0] * plan->dims[1] * plan->dims[2];
-    const size_t bytes = (size_t)N * sizeof(float2);
+    const size_t bytes = (size_t)N * (plan->dtype == CROFT_C2C_F64 ? sizeof(double2) : sizeof(float2));
     const char* a = (const char*)in;
     const char* b = (const char*)out;
     if (a != b && a < b + bytes && b < a + bytes) return CROFT_ERR_INVALID_ARG;
@@ -582,8 +620,9 @@ static croft_status exec_dir(croft_plan plan, const void* in, void* out, void* s
         PassLaunch L = plan->passes[i];
         L.args.isign = isign;
         L.pargs.isign = isign;
-        const float2* src = (L.src_in ? (const float2*)in : (const float2*)out) + L.offset;
-        float2* dst = (float2*)out + L.offset;
+        const size_t es = L.f64 ? sizeof(double2) : sizeof(float2);
+        const char* src = (L.src_in ? (const char*)in : (const char*)out) + (size_t)L.offset * es;
+        char* dst = (char*)out + (size_t)L.offset * es;
         cudaError_t e = launch_pass(L, src, dst, s);
         if (e != cudaSuccess) { cudaGetLastError(); return CROFT_ERR_CUDA; }
         const bool group_end = (i + 1 == plan->passes.size()) || plan->passes[i + 1].group != L.group;

@@ -53,7 +53,8 @@ size_t stream_state_bytes(const StreamState* st) { return st ? kSlots * st->byte
 static croft_status stream_state_create(croft_plan plan, StreamState** out) {
     StreamState* st = new (std::nothrow) StreamState();
     if (!st) return CROFT_ERR_OOM;
-    st->bytes = (size_t)plan->dims[0] * plan->dims[1] * plan->dims[2] * sizeof(float2);
+    st->bytes = (size_t)plan->dims[0] * plan->dims[1] * plan->dims[2] *
+                (plan->dtype == CROFT_C2C_F64 ? sizeof(double2) : sizeof(float2));
     for (int k = 0; k < kSlots; ++k)
         if (dev_alloc((void**)&st->slot[k], st->bytes) != cudaSuccess) {
             cudaGetLastError();
