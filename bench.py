@@ -216,7 +216,7 @@ def _flush(flush):
     flush.fill_(1.0)
 
 
-def time_transform(croft, torch, stream, flush, plan, run_fwd, run_bwd, reps=5, warm=2):
+def time_transform(croft, torch, stream, flush, plan, run_fwd, run_bwd, reps=5, warm=2):  # noqa: PLR0913
     """Median device ms of forward and backward (L2 flushed before each) and mean per-pass ms."""
     fw, bw, passes = [], [], []
     for i in range(warm + reps):
@@ -282,6 +282,33 @@ def measure_rows(croft, torch, dev, stream, flush, peak):
                       "pass_ms": pass_ms, "dominant_pass_gbs": 16.0 * n / (pass_ms[dom] * 1e-3) / 1e9,
                       "dominant_pass_frac": (16.0 * n / (pass_ms[dom] * 1e-3) / 1e9) / peak,
                       "roundtrip_rel_l2": rt, "plan": desc}
+        del x, y, z
+    # complex128 at the paper's sizes (its Tables 1 and 3 time one double-complex forward transform)
+    paper = {128: {"croft_best_s": 0.014, "croft_best_cores": 32, "fftw3_best_s": 0.019, "fftw3_best_cores": 32,
+                   "source": "Table 1"},
+             1024: {"croft_best_s": 1.2722, "croft_best_cores": 512, "fftw3_best_s": 4.7209, "fftw3_best_cores": 256,
+                    "source": "Table 3"}}
+    for n in (128, 1024):
+        shape = (n, n, n)
+        x = torch.complex(torch.rand(shape, device=dev, dtype=torch.float64, generator=gen) * 2 - 1,
+                          torch.rand(shape, device=dev, dtype=torch.float64, generator=gen) * 2 - 1)
+        y = torch.empty_like(x)
+        z = torch.empty_like(x)
+        with croft.Plan(*shape, dtype=croft.CROFT_C2C_F64) as p:
+            croft.croft_plan_set_timing(p.handle, True)
+            sh = stream.cuda_stream
+            f_ms, b_ms, pass_ms = time_transform(
+                croft, torch, stream, flush, p.handle,
+                lambda: croft.croft_exec_forward(p.handle, x, y, sh),
+                lambda: croft.croft_exec_backward(p.handle, y, z, sh), reps=3 if n > 512 else 5, warm=1)
+        stream.synchronize()
+        nn = n ** 3
+        rt = float(torch.linalg.vector_norm((z - nn * x).flatten()) / torch.linalg.vector_norm((nn * x).flatten()))
+        rows[f"f64_{n}"] = {"shape": list(shape), "dtype": "f64", "ms_fwd": f_ms, "ms_bwd": b_ms,
+                            "gflops_fwd": nominal_flops(shape) / (f_ms * 1e-3) / 1e9, "pass_ms": pass_ms,
+                            "roundtrip_rel_l2": rt,
+                            "paper_context": dict(paper[n], speedup_vs_croft_best=paper[n]["croft_best_s"] / (f_ms * 1e-3),
+                                                  speedup_vs_fftw3_best=paper[n]["fftw3_best_s"] / (f_ms * 1e-3))}
         del x, y, z
     # the batch of 96 uneven PME meshes (seed-3 sizes), one persistent launch vs per-grid plans
     rng = np.random.default_rng(3)
