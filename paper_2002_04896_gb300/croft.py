@@ -122,8 +122,12 @@ def _stream_ptr(stream) -> int:
     return int(stream.cuda_stream)
 
 
-def _ptr(x, numel=None, complex128=False) -> int:
-    """Device address of a raw pointer (int) or of a C-contiguous complex64 (complex128) CUDA tensor."""
+def _ptr(x, numel=None, complex128=None) -> int:
+    """Device address of a raw pointer (int) or of a C-contiguous complex CUDA tensor.
+
+    complex128: True / False require that dtype; None (the raw entry points) accepts
+    complex64 and complex128 and leaves matching the plan's dtype to the caller.
+    """
     if x is None:
         return 0
     if isinstance(x, int):
@@ -133,9 +137,10 @@ def _ptr(x, numel=None, complex128=False) -> int:
         raise TypeError("expected a torch CUDA tensor or an integer device address")
     if not x.is_cuda:
         raise ValueError("croft: tensors must live on a CUDA device")
-    want = torch.complex128 if complex128 else torch.complex64
-    if x.dtype != want:
-        raise ValueError(f"croft: expected {want}, got {x.dtype}")
+    allowed = ((torch.complex64, torch.complex128) if complex128 is None
+               else ((torch.complex128,) if complex128 else (torch.complex64,)))
+    if x.dtype not in allowed:
+        raise ValueError(f"croft: expected {' or '.join(map(str, allowed))}, got {x.dtype}")
     if not x.is_contiguous():
         raise ValueError("croft: tensors must be C-contiguous in (nx, ny, nz) order")
     if numel is not None and x.numel() != numel:
