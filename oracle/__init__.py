@@ -1,4 +1,5 @@
-"""CPU oracle for the 3D C2C DFT (test infrastructure; see ``oracle.direct_dft``).
+"""CPU oracle for the 3D C2C DFT and the PME reciprocal-space convolution (test
+infrastructure; see ``oracle.direct_dft`` and ``oracle.convolution``).
 
 Only ``tests/``, ``__graft_entry__.smoke()`` and ``bench.py``'s CPU-baseline
 and reference legs may import this package.  The CUDA library never does.
@@ -16,3 +17,4 @@ from .direct_dft import (  # noqa: F401
     forward,
     rel_l2,
 )
+from .convolution import convolve  # noqa: F401,E402

@@ -22,6 +22,9 @@ Recipes (one per workload):
   charge).  The imaginary part is zero.
 * ``pme_batch(count, seed)``: the batch of uneven grids (each axis length
   drawn from a fixed menu, 2 * U{10000..100000} charges per grid).
+* ``pme_influence(shape)``: the real reciprocal-space influence function that
+  a smooth-PME code multiplies the transformed charge grid by before the
+  backward transform (no random draws; a fixed function of the mesh).
 """
 
 from __future__ import annotations
@@ -34,6 +37,7 @@ __all__ = [
     "pme_charge_grid",
     "pme_batch",
     "config_input",
+    "pme_influence",
     "BATCH_AXIS_CHOICES",
 ]
 
@@ -122,6 +126,40 @@ def pme_batch(count: int = 96, seed: int = 3, choices=BATCH_AXIS_CHOICES):
     for g in range(count):
         grids.append(pme_charge_grid(tuple(int(d) for d in dims[g]), int(m[g]), rng))
     return [tuple(int(d) for d in row) for row in dims], grids
+
+
+def pme_influence(shape, spacing: float = 0.1, beta: float = 3.12, dtype=np.float32) -> np.ndarray:
+    """Smooth-PME influence function G(k) on an (nx, ny, nz) mesh, indexed like the transform's output.
+
+    Orthorhombic box with mesh spacing ``spacing`` on every axis (box side
+    L_a = K_a * spacing) and Ewald splitting parameter ``beta`` (1/length).
+    With the signed frequency m_a = k_a (k_a <= K_a/2) or k_a - K_a, the
+    reciprocal vector f_a = m_a / L_a and V = L_x L_y L_z:
+
+        G(k) = exp(-pi^2 |f|^2 / beta^2) / (pi V |f|^2) * prod_a |b_a(k_a)|^2,   G(0) = 0,
+
+    where 1 / |b_a(k)|^2 = |sum_{t=0..2} M4(t+1) exp(2 pi i k t / K_a)|^2 with the
+    order-4 cardinal B-spline values M4(1) = M4(3) = 1/6, M4(2) = 2/3 (the
+    interpolation correction that goes with ``bspline4_weights``).  G is real
+    and even (G(-k) = G(k)).  Computed in float64, cast to ``dtype`` at the end.
+    """
+    shape = tuple(int(s) for s in shape)
+    axes_f2 = []
+    axes_b2 = []
+    for k_len in shape:
+        k = np.arange(k_len, dtype=np.int64)
+        m = np.where(k <= k_len // 2, k, k - k_len).astype(np.float64)
+        axes_f2.append((m / (k_len * spacing)) ** 2)
+        ph = 2.0 * np.pi * k.astype(np.float64) / k_len
+        den = (1.0 / 6.0) + (2.0 / 3.0) * np.exp(1j * ph) + (1.0 / 6.0) * np.exp(2j * ph)
+        axes_b2.append(1.0 / np.abs(den) ** 2)
+    f2 = axes_f2[0][:, None, None] + axes_f2[1][None, :, None] + axes_f2[2][None, None, :]
+    b2 = axes_b2[0][:, None, None] * axes_b2[1][None, :, None] * axes_b2[2][None, None, :]
+    vol = float(np.prod([k_len * spacing for k_len in shape]))
+    with np.errstate(divide="ignore", invalid="ignore"):
+        g = np.exp(-(np.pi ** 2) * f2 / beta ** 2) / (np.pi * vol * f2) * b2
+    g[0, 0, 0] = 0.0
+    return g.astype(dtype)
 
 
 def config_input(name: str):
