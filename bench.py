@@ -283,6 +283,55 @@ def measure_rows(croft, torch, dev, stream, flush, peak):
                       "dominant_pass_frac": (16.0 * n / (pass_ms[dom] * 1e-3) / 1e9) / peak,
                       "roundtrip_rel_l2": rt, "plan": desc}
         del x, y, z
+    # PME reciprocal-space convolution B(G * F(x)) on 256^3 with the smooth-PME influence function:
+    # croft_exec_convolve (last-axis forward * G * backward fused) vs forward, a torch multiply, backward
+    shape = (256, 256, 256)
+    n = math.prod(shape)
+    x = grid(shape)
+    y = torch.empty_like(x)
+    y2 = torch.empty_like(x)
+    g = torch.from_numpy(S.pme_influence(shape)).to(dev)
+    with croft.Plan(*shape) as p:
+        croft.croft_plan_set_timing(p.handle, True)
+        sh = stream.cuda_stream
+        t_conv, t_sep, pts = [], [], []
+        for i in range(2 + 5):
+            for kind in ("conv", "sep"):
+                with torch.cuda.stream(stream):
+                    _flush(flush)
+                    a = torch.cuda.Event(enable_timing=True)
+                    b = torch.cuda.Event(enable_timing=True)
+                    a.record(stream)
+                    if kind == "conv":
+                        croft.croft_exec_convolve(p.handle, x, y, g, sh)
+                    else:
+                        croft.croft_exec_forward(p.handle, x, y2, sh)
+                        y2.mul_(g)
+                        croft.croft_exec_backward(p.handle, y2, y2, sh)
+                    b.record(stream)
+                pt = croft.croft_plan_pass_times(p.handle, 16) if kind == "conv" else None
+                stream.synchronize()
+                if i >= 2:
+                    (t_conv if kind == "conv" else t_sep).append(a.elapsed_time(b))
+                    if pt:
+                        pts.append(pt)
+        desc = p.describe()
+    stream.synchronize()
+    diff = float(torch.linalg.vector_norm((y - y2).flatten()) / torch.linalg.vector_norm(y2.flatten()))
+    tc_ms, ts_ms = statistics.median(t_conv), statistics.median(t_sep)
+    pass_ms = [statistics.mean(q[i] for q in pts) for i in range(len(pts[0]))] if pts else []
+    rows["pme256_convolve"] = {
+        "shape": list(shape), "ms": tc_ms, "gflops": 2 * nominal_flops(shape) / (tc_ms * 1e-3) / 1e9,
+        "pass_ms": pass_ms,
+        "fused_pass_ms": pass_ms[len(pass_ms) // 2] if pass_ms else None,
+        "fused_pass_frac": ((20.0 * n / (pass_ms[len(pass_ms) // 2] * 1e-3) / 1e9) / peak) if pass_ms else None,
+        "hbm_frac_compulsory": (20.0 * n / (tc_ms * 1e-3) / 1e9) / peak,
+        "hbm_frac_passes": (84.0 * n / (tc_ms * 1e-3) / 1e9) / peak,
+        "separate_ms": ts_ms, "speedup_vs_separate": ts_ms / tc_ms, "rel_diff_vs_separate": diff,
+        "plan": desc,
+        "notes": "fused: 4 plain passes (16N B each) + 1 fused pass (20N B: grid in/out + G); "
+                 "separate: 6 passes + torch's multiply (20N B)"}
+    del x, y, y2, g
     # complex128 at the paper's sizes (its Tables 1 and 3 time one double-complex forward transform)
     paper = {128: {"croft_best_s": 0.014, "croft_best_cores": 32, "fftw3_best_s": 0.019, "fftw3_best_cores": 32,
                    "source": "Table 1"},

@@ -242,6 +242,39 @@ croft_status croft_exec_forward(croft_plan plan, const void* in, void* out, void
 croft_status croft_exec_backward(croft_plan plan, const void* in, void* out, void* stream);
 
 /*
+ * croft_exec_convolve - the reciprocal-space step of particle-mesh Ewald, the
+ * application that motivates the paper (Sec. 1):
+ *
+ *     out = B(G * F(in)),   F = Eq. (1), B = Eq. (2) with exponent + and no 1/N,
+ *
+ * i.e. the circular convolution of `in` with B(G).  G is a real array indexed
+ * like F's output (k = (kx, ky, kz), same layout as the grid); for PME it is
+ * the influence function.
+ *
+ * The forward transform runs its passes up to the last axis; that axis's
+ * forward 1D FFT, the multiply by G and its backward 1D FFT run fused in one
+ * kernel (one HBM round trip instead of three); then the backward passes of
+ * the other axes.  A 3D grid takes 5 launches.  Plans whose last pass cannot
+ * take the fusion (a grid of one point, a last pass that is a fused yz-plane
+ * or a tensor-core pass) run F, a separate multiply and B instead.  There is
+ * no counterpart of this entry point in the paper beyond the application it
+ * describes.
+ *
+ *   plan : a single-grid plan (any dtype and schedule).
+ *   in, out : device pointers to nx*ny*nz complex elements of the plan's dtype,
+ *       16-byte aligned; in == out is allowed, partial overlap is not.
+ *   g : device pointer to nx*ny*nz reals (float for the complex64 dtypes,
+ *       double for CROFT_C2C_F64), aligned to its element size; must not
+ *       overlap `out`.  Read only.
+ *   stream : cudaStream_t or NULL.  Asynchronous, stream-ordered; allocates
+ *       nothing.
+ * Returns CROFT_OK, CROFT_ERR_INVALID_ARG (NULL plan/pointer, batched plan,
+ * misaligned pointer, overlap) or CROFT_ERR_CUDA.  With timing enabled,
+ * croft_plan_pass_times reports one time per launch group in execution order.
+ */
+croft_status croft_exec_convolve(croft_plan plan, const void* in, void* out, const void* g, void* stream);
+
+/*
  * croft_exec_host_pipeline - transform `count` HOST-resident grids, streaming
  * them through the GPU.  For grid i: copy host_in[i] to the device, apply the
  * requested operations in place (CROFT_OP_FORWARD: Eq. 1; CROFT_OP_BACKWARD:

@@ -1,7 +1,8 @@
 """Build libcroft.so (the C-ABI library) in-tree with nvcc for sm_103a.
 
 Translation units compile in parallel; the pass-kernel instantiations are split
-into four size groups (``croft_kernels.cu`` compiled with ``-DCROFT_GROUP=g``).
+into four size groups (``croft_kernels.cu`` compiled with ``-DCROFT_GROUP=g``),
+the fused convolution pass into five (``croft_conv.cu``, ``-DCROFT_CONV_GROUP=g``).
 Objects go to ``paper_2002_04896_gb300/_build/`` and are rebuilt only when a
 source or header is newer than the object.
 """
@@ -44,8 +45,11 @@ def _units():
     for g in range(2):
         units.append((os.path.join(CSRC, "croft_pipe.cu"), os.path.join(BUILD, f"croft_pipe_g{g}.o"),
                       [f"-DCROFT_PIPE_GROUP={g}"]))
+    for g in range(5):
+        units.append((os.path.join(CSRC, "croft_conv.cu"), os.path.join(BUILD, f"croft_conv_g{g}.o"),
+                      [f"-DCROFT_CONV_GROUP={g}"]))
     for src in sorted(glob.glob(os.path.join(CSRC, "*.cu"))):
-        if os.path.basename(src) in ("croft_kernels.cu", "croft_pipe.cu"):
+        if os.path.basename(src) in ("croft_kernels.cu", "croft_pipe.cu", "croft_conv.cu"):
             continue
         obj = os.path.join(BUILD, os.path.basename(src)[:-3] + ".o")
         units.append((src, obj, []))

@@ -81,6 +81,7 @@ _debug_fail_allocation = _sig("croft_debug_fail_allocation", None, [_I])
 _debug_live_allocations = _sig("croft_debug_live_allocations", ctypes.c_long, [])
 _exec_batched_noalloc = _sig("croft_exec_batched_noalloc", _I,
                              [_I, ctypes.POINTER(_I), ctypes.POINTER(_P), ctypes.POINTER(_P), _I, _P])
+_exec_convolve = _sig("croft_exec_convolve", _I, [_P, _P, _P, _P, _P])
 _twiddle_table = _sig("croft_twiddle_table", _I, [_I, ctypes.POINTER(_I), _I, ctypes.POINTER(ctypes.c_float)])
 
 LIBRARY_PATH = _LIB_PATH
@@ -91,7 +92,7 @@ EXPORTED = [
     "croft_twiddle_table", "croft_plan_create_batched", "croft_plan_create_batched_mode",
     "croft_exec_batched_forward", "croft_exec_batched_backward", "croft_plan_set_wait_limit",
     "croft_plan_set_test_unsatisfiable_wait", "croft_exec_batched_noalloc", "croft_debug_fail_allocation",
-    "croft_debug_live_allocations", "croft_exec_host_pipeline",
+    "croft_debug_live_allocations", "croft_exec_host_pipeline", "croft_exec_convolve",
 ]
 
 
@@ -169,6 +170,29 @@ def croft_exec_backward_status(plan: int, inp, out, stream=None) -> int:
     return _exec_backward(plan, _ptr(inp), _ptr(out), _stream_ptr(stream))
 
 
+def _real_ptr(g, numel=None, f64=None) -> int:
+    """Device address of a raw pointer (int) or of a C-contiguous real CUDA tensor (the influence function)."""
+    if g is None:
+        return 0
+    if isinstance(g, int):
+        return g
+    import torch
+    if not isinstance(g, torch.Tensor) or not g.is_cuda:
+        raise ValueError("croft: the influence function must be a CUDA tensor")
+    allowed = ((torch.float32, torch.float64) if f64 is None else ((torch.float64,) if f64 else (torch.float32,)))
+    if g.dtype not in allowed:
+        raise ValueError(f"croft: expected {' or '.join(map(str, allowed))} for the influence function, got {g.dtype}")
+    if not g.is_contiguous():
+        raise ValueError("croft: the influence function must be C-contiguous in (kx, ky, kz) order")
+    if numel is not None and g.numel() != numel:
+        raise ValueError(f"croft: influence function has {g.numel()} elements, plan expects {numel}")
+    return int(g.data_ptr())
+
+
+def croft_exec_convolve_status(plan: int, inp, out, g, stream=None) -> int:
+    return _exec_convolve(plan, _ptr(inp), _ptr(out), _real_ptr(g), _stream_ptr(stream))
+
+
 # ---------------------------------------------------------------------------
 # raising wrappers with the C names
 # ---------------------------------------------------------------------------
@@ -191,6 +215,11 @@ def croft_exec_forward(plan: int, inp, out, stream=None) -> None:
 
 def croft_exec_backward(plan: int, inp, out, stream=None) -> None:
     _check(croft_exec_backward_status(plan, inp, out, stream), "croft_exec_backward")
+
+
+def croft_exec_convolve(plan: int, inp, out, g, stream=None) -> None:
+    """out = B(G * F(in)): the PME reciprocal-space convolution (see include/croft.h)."""
+    _check(croft_exec_convolve_status(plan, inp, out, g, stream), "croft_exec_convolve")
 
 
 def croft_plan_workspace_bytes(plan: int) -> int:
@@ -418,6 +447,13 @@ class Plan:
     def backward(self, inp, out=None, stream=None):
         pi, po, out = self._out(inp, out)
         croft_exec_backward(self.handle, pi, po, stream)
+        return out
+
+    def convolve(self, inp, g, out=None, stream=None):
+        """B(G * F(inp)) with a real influence function g of the grid's shape (float32, or float64 for complex128)."""
+        pi, po, out = self._out(inp, out)
+        n = self.shape[0] * self.shape[1] * self.shape[2]
+        croft_exec_convolve(self.handle, pi, po, _real_ptr(g, n, self.dtype == CROFT_C2C_F64), stream)
         return out
 
     def describe(self) -> str:

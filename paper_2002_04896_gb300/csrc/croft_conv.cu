@@ -1,0 +1,50 @@
+// croft_conv.cu - instantiates the fused convolution pass (croft_conv_kernel.cuh).
+// Compiled five times: -DCROFT_CONV_GROUP=0..3 take the four complex64 size groups
+// of croft_sizes.h; 4 takes the complex128 lengths and the multiply-only kernels.
+#include "croft_conv_kernel.cuh"
+#include "croft_sizes.h"
+
+#ifndef CROFT_CONV_GROUP
+#error "compile with -DCROFT_CONV_GROUP=<0..4>"
+#endif
+
+namespace croft {
+
+#define CROFT_CONV_CASE(N) \
+    case N: return croft_conv_kernel<N, float2>;
+
+#define CROFT_CAT_(a, b) a##b
+#define CROFT_CAT(a, b) CROFT_CAT_(a, b)
+
+#if CROFT_CONV_GROUP < 4
+conv_fn CROFT_CAT(lookup_conv_kernel_group_, CROFT_CONV_GROUP)(int n) {
+    switch (n) {
+        CROFT_CAT(CROFT_SIZES_, CROFT_CONV_GROUP)(CROFT_CONV_CASE)
+        default: return nullptr;
+    }
+}
+#else
+// complex128: the lengths of the complex128 pass kernels
+conv64_fn conv64_kernel_for(int n) {
+#define CROFT_CONV64_CASE(N) \
+    case N: return croft_conv_kernel<N, double2>;
+    switch (n) {
+        CROFT_SIZES64(CROFT_CONV64_CASE)
+        default: return nullptr;
+    }
+#undef CROFT_CONV64_CASE
+}
+
+cudaError_t launch_scale(const void* in, void* out, const void* g, long long n, bool f64, cudaStream_t s) {
+    if (n <= 0) return cudaSuccess;
+    long long blocks = (n + 255) / 256;
+    if (blocks > 152LL * 8) blocks = 152LL * 8;
+    if (f64)
+        croft_scale_kernel<double2><<<(int)blocks, 256, 0, s>>>((const double2*)in, (double2*)out, (const double*)g, n);
+    else
+        croft_scale_kernel<float2><<<(int)blocks, 256, 0, s>>>((const float2*)in, (float2*)out, (const float*)g, n);
+    return cudaGetLastError();
+}
+#endif
+
+}  // namespace croft

@@ -1,0 +1,120 @@
+// croft_conv_kernel.cuh - the reciprocal-space step of PME fused into one pass:
+// the last forward 1D FFT, the multiplication by the influence function G and
+// the first backward 1D FFT, all along the same axis while the column tile is
+// on chip.
+//
+// Paper mapping.  The paper's application (Sec. 1) is particle-mesh Ewald: the
+// charge grid is transformed forward (Eq. 1), multiplied point by point by a
+// real influence function and transformed back (Eq. 2, unnormalised here).
+// Because the three 1D transforms of a 3D DFT commute (separability, Sec. 2.1),
+// the backward transform may start with the axis the forward one ended with.
+// Doing both on that axis inside one CTA removes one HBM round trip of the
+// grid (the forward pass's write and the backward pass's read) and the
+// separate multiply pass; the other axes run as ordinary passes.
+//
+// Tile: W adjacent columns of the axis (COL layout, croft_internal.h), the
+// matching W columns of G (real, same layout as the grid) and the twiddles.
+// G is copied to shared memory with cp.async at the start, so its latency
+// hides behind the forward stages.  The backward transform is conj(F(conj(.))):
+// the last forward stage stores conj(G * Y) into the tile, the forward stages
+// run again on it, and the final store conjugates.
+#pragma once
+#include "croft_fft_core.cuh"
+#include "croft_internal.h"
+
+namespace croft {
+
+// Store of the last forward stage: element a of this column times G(a), conjugated.
+template <class C>
+struct ScaleConjCol {
+    using value_type = C;
+    using R = typename CxScalar<C>::T;
+    C* s;        // tile + c
+    const R* g;  // G tile + c
+    int W;
+    __device__ __forceinline__ void store(int a, C v) const {
+        const R ga = g[a * W];
+        s[a * W] = mkc<C>(v.x * ga, -(v.y * ga));
+    }
+};
+
+template <class R>
+__device__ __forceinline__ void conv_cp_async(R* dst_smem, const R* src) {
+    const uint32_t d = (uint32_t)__cvta_generic_to_shared(dst_smem);
+    if constexpr (sizeof(R) == 4)
+        asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(d), "l"(src) : "memory");
+    else
+        asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"(d), "l"(src) : "memory");
+}
+
+// Shared memory: [twiddles: tw_pad][tile: N x W complex][G tile: N x W real].
+template <int N, class C = float2>
+__global__ void __launch_bounds__(512) croft_conv_kernel(const C* in, C* out, const typename CxScalar<C>::T* g,
+                                                         const __grid_constant__ PassArgs A) {
+    using R = typename CxScalar<C>::T;
+    constexpr int T = croft_threads_per_pencil(N);
+    constexpr CroftSched sc = croft_make_sched(N);
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    C* stw = reinterpret_cast<C*>(smem_raw);
+    C* tile = stw + A.tw_pad;
+    R* gtile = reinterpret_cast<R*>(tile + (long long)N * A.W);
+    const C* twg;
+    if constexpr (sizeof(C) == 16) twg = A.tw64;
+    else twg = A.tw;
+
+    const int c = threadIdx.x % A.W;
+    const int lane = threadIdx.x / A.W;
+    const long long col = (long long)blockIdx.x * A.W + c;
+    const bool ok = col < A.ncols;
+    const long long b = col / A.M;
+    const long long m = col - b * A.M;
+    const long long base = b * (long long)N * A.M + m;
+
+    if (ok)
+        for (int a = lane; a < N; a += T) conv_cp_async(gtile + a * A.W + c, g + base + (long long)a * A.M);
+    asm volatile("cp.async.commit_group;" ::: "memory");
+    if (sc.count > 1)
+        for (int i = threadIdx.x; i < N - 1; i += blockDim.x) stw[i] = twg[i];
+
+    const GlobalInT<C> src{in + base, A.M, 1.f};
+    const SmemColT<C> work{tile + c, A.W};
+    const ScaleConjCol<C> scaled{tile + c, gtile + c, A.W};
+    const GlobalOutT<C> dst{out + base, A.M, -1.f};
+
+    // forward transform of the column; its last stage leaves conj(G * Y) in the tile.
+    // (The barrier inside the last stage also publishes every thread's G copies.)
+    if constexpr (sc.count == 1) {
+        asm volatile("cp.async.wait_all;" ::: "memory");
+        fft_stage<N, 0, T>(src, CtaBarrier{}, scaled, stw, lane, ok);
+    } else {
+        fft_stage<N, 0, T>(src, NoBarrier{}, work, stw, lane, ok);
+        __syncthreads();
+        smem_stages<N, 1, sc.count - 1, T>(work, stw, lane, ok);
+        asm volatile("cp.async.wait_all;" ::: "memory");
+        fft_stage<N, sc.count - 1, T>(work, CtaBarrier{}, scaled, stw, lane, ok);
+    }
+    __syncthreads();
+    // backward transform along the same axis: forward stages on the conjugated tile, conjugated store
+    if constexpr (sc.count == 1) {
+        fft_stage<N, 0, T>(work, NoBarrier{}, dst, stw, lane, ok);
+    } else {
+        fft_stage<N, 0, T>(work, CtaBarrier{}, work, stw, lane, ok);
+        __syncthreads();
+        smem_stages<N, 1, sc.count - 1, T>(work, stw, lane, ok);
+        fft_stage<N, sc.count - 1, T>(work, NoBarrier{}, dst, stw, lane, ok);
+    }
+}
+
+// out[i] = in[i] * g[i] (the multiply on its own, for plans whose last pass cannot
+// take it: a grid of one point, a last pass that is a fused plane or a
+// tensor-core pass).  Grid-stride loop.
+template <class C>
+__global__ void croft_scale_kernel(const C* in, C* out, const typename CxScalar<C>::T* g, long long n) {
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+        const C v = in[i];
+        const typename CxScalar<C>::T s = g[i];
+        out[i] = mkc<C>(v.x * s, v.y * s);
+    }
+}
+
+}  // namespace croft

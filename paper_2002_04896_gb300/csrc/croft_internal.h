@@ -39,6 +39,9 @@ struct PlaneArgs {
 
 typedef void (*pass_fn)(const float2*, float2*, const PassArgs);
 typedef void (*pass64_fn)(const double2*, double2*, const PassArgs);
+// fused convolution pass (croft_conv_kernel.cuh): the extra operand is the real influence function
+typedef void (*conv_fn)(const float2*, float2*, const float*, const PassArgs);
+typedef void (*conv64_fn)(const double2*, double2*, const double*, const PassArgs);
 
 // TMA-pipelined persistent pass (croft_pipe_kernel.cuh).
 struct PipeArgs {
@@ -110,12 +113,24 @@ void host_free(void* p);
 // croft_kernels64.cu: complex128 pass kernels (NULL when n has no instantiation)
 pass64_fn pass64_kernel_for(int layout, int n);
 
+// croft_conv.cu: fused convolution pass kernels (NULL when n has no instantiation)
+conv_fn lookup_conv_kernel_group_0(int n);
+conv_fn lookup_conv_kernel_group_1(int n);
+conv_fn lookup_conv_kernel_group_2(int n);
+conv_fn lookup_conv_kernel_group_3(int n);
+conv64_fn conv64_kernel_for(int n);
+// out = in * g elementwise (complex times real), n elements
+cudaError_t launch_scale(const void* in, void* out, const void* g, long long n, bool f64, cudaStream_t s);
+
 // croft_passes.cu
 pass_fn pass_kernel_for(int layout, int n);
+conv_fn conv_kernel_for(int n);
 pipe_fn pipe_kernel_for(int layout, int n);
 int pipe_blocks_per_sm(const PassLaunch& L);
 cudaError_t prepare_pass(const PassLaunch& L);  // once per plan: shared-memory / cluster opt-ins, occupancy check
 cudaError_t launch_pass(const PassLaunch& L, const void* in, void* out, cudaStream_t s);
+// the fused convolution pass (args/shape of a COL pass; g: the real influence function)
+cudaError_t launch_conv(const PassLaunch& L, const void* in, void* out, const void* g, cudaStream_t s);
 int active_clusters(const PassLaunch& L);  // co-resident clusters of a plane pass (0 for axis passes)
 
 }  // namespace croft

@@ -7,11 +7,9 @@
 // double-complex runs, not as a fast path.  Lengths: every power of two up to
 // 1024 and a few mixed-radix ones.
 #include "croft_pass_kernel.cuh"
+#include "croft_sizes.h"
 
 namespace croft {
-
-#define CROFT_SIZES64(X) \
-    X(2) X(3) X(4) X(5) X(6) X(8) X(10) X(12) X(15) X(16) X(32) X(48) X(60) X(64) X(96) X(120) X(128) X(256) X(512) X(1024)
 
 pass64_fn pass64_kernel_for(int layout, int n) {
 #define CROFT_CASE64(N)                                                                 \

@@ -66,6 +66,14 @@ pass_fn pass_kernel_for(int layout, int n) {
     return f;
 }
 
+conv_fn conv_kernel_for(int n) {
+    conv_fn f = lookup_conv_kernel_group_0(n);
+    if (!f) f = lookup_conv_kernel_group_1(n);
+    if (!f) f = lookup_conv_kernel_group_2(n);
+    if (!f) f = lookup_conv_kernel_group_3(n);
+    return f;
+}
+
 static cudaLaunchConfig_t plane_config(const PassLaunch& L, cudaStream_t s, cudaLaunchAttribute* attr) {
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3((unsigned)L.grid, 1, 1);
@@ -143,6 +151,19 @@ cudaError_t launch_pass(const PassLaunch& L, const void* vin, void* vout, cudaSt
     pass_fn f = L.tc ? tc_pass_kernel_for(L.layout, L.args.n) : pass_kernel_for(L.layout, L.args.n);
     if (!f) return cudaErrorInvalidValue;
     f<<<L.grid, L.block, L.smem, s>>>(in, out, L.args);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_conv(const PassLaunch& L, const void* in, void* out, const void* g, cudaStream_t s) {
+    if (L.f64) {
+        conv64_fn f = conv64_kernel_for(L.args.n);
+        if (!f) return cudaErrorInvalidValue;
+        f<<<L.grid, L.block, L.smem, s>>>((const double2*)in, (double2*)out, (const double*)g, L.args);
+    } else {
+        conv_fn f = conv_kernel_for(L.args.n);
+        if (!f) return cudaErrorInvalidValue;
+        f<<<L.grid, L.block, L.smem, s>>>((const float2*)in, (float2*)out, (const float*)g, L.args);
+    }
     return cudaGetLastError();
 }
 

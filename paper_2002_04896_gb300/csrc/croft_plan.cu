@@ -359,6 +359,45 @@ static croft_status add_plane_pass(croft_plan p, const PlaneKernel* pk) {
     return CROFT_OK;
 }
 
+// Fused convolution pass for croft_exec_convolve: it replaces the plan's last pass
+// when that pass is a plain (CUDA-core, non-pipelined) axis pass over the whole grid
+// that forms a logical pass of its own; otherwise convolve runs F, multiply, B.
+static void plan_conv(croft_plan p) {
+    p->conv_fused = false;
+    p->conv_axis = -1;
+    if (p->passes.empty()) return;
+    const size_t last = p->passes.size() - 1;
+    const PassLaunch& Lp = p->passes[last];
+    const int axis = p->pass_axis[last];
+    if (Lp.kind != PASS_AXIS || Lp.offset != 0 || axis < 0 || axis > 2 || Lp.tc || p->axis_tc[axis]) return;
+    if (last > 0 && p->passes[last - 1].group == Lp.group) return;
+    const bool f64 = p->dtype == CROFT_C2C_F64;
+    const int n = p->dims[axis];
+    const long long N = (long long)p->dims[0] * p->dims[1] * p->dims[2];
+    const long long M = (axis == 2) ? 1 : (axis == 1 ? (long long)p->dims[2] : (long long)p->dims[1] * p->dims[2]);
+    if (f64 ? !conv64_kernel_for(n) : !conv_kernel_for(n)) return;
+    PassLaunch L;
+    if (!shape_pass(L, LAYOUT_COL, n, M, N / n, false, f64)) return;
+    const long long es = f64 ? 16 : 8;
+    const long long smem = ((long long)L.args.tw_pad + (long long)n * L.args.W) * es + (long long)n * L.args.W * (es / 2);
+    if (smem > g_max_smem) return;
+    L.smem = (int)smem;
+    L.kind = PASS_AXIS;
+    L.args.tw = p->tw_dev[axis];
+    L.args.tw64 = f64 ? (const double2*)p->tw_dev[axis] : nullptr;
+    L.args.status = p->d_status;
+    L.group = Lp.group;
+    L.src_in = Lp.src_in;
+    const void* fn = f64 ? (const void*)conv64_kernel_for(n) : (const void*)conv_kernel_for(n);
+    if (L.smem > 48 * 1024 && cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, L.smem) != cudaSuccess) {
+        cudaGetLastError();
+        return;
+    }
+    p->conv = L;
+    p->conv_axis = axis;
+    p->conv_fused = true;
+}
+
 static croft_status create_impl(croft_plan* out, int nx, int ny, int nz, croft_dtype dtype, croft_schedule sched) {
     if (!out) return CROFT_ERR_INVALID_ARG;
     *out = NULL;
@@ -397,6 +436,8 @@ static croft_status create_impl(croft_plan* out, int nx, int ny, int nz, croft_d
     p->stream = NULL;
     p->tc_b = NULL;
     p->d_status = NULL;
+    p->conv_fused = false;
+    p->conv_axis = -1;
     const bool want_tc = dtype == CROFT_C2C_F32_TC_BF16X3;
     for (int axis = 0; axis < 3; ++axis) {
         const long long M = (axis == 2) ? 1 : (axis == 1 ? (long long)nz : (long long)ny * nz);
@@ -471,6 +512,7 @@ static croft_status create_impl(croft_plan* out, int nx, int ny, int nz, croft_d
         if (planes > nx) planes = nx;
         croft_status st = add_slab_passes(p, planes);
         if (st != CROFT_OK) return fail(p, st);
+        plan_conv(p);
         *out = p;
         return CROFT_OK;
     }
@@ -483,6 +525,7 @@ static croft_status create_impl(croft_plan* out, int nx, int ny, int nz, croft_d
         croft_status st = add_axis_pass(p, axes[i]);
         if (st != CROFT_OK) return fail(p, st);
     }
+    plan_conv(p);
     const char* log = getenv("CROFT_LOG");
     if (log && log[0] == '1') {
         char buf[2048];
@@ -531,6 +574,14 @@ int croft_plan_describe(croft_plan plan, char* buf, int cap) {
         snprintf(tmp, sizeof(tmp), " T=%d W=%d block=%d grid=%d smem=%d", L.T, L.args.W, L.block, L.grid, L.smem);
         s += tmp;
     }
+    if (plan->conv_fused) {
+        const PassLaunch& L = plan->conv;
+        snprintf(tmp, sizeof(tmp), " | convolve: %s fwd*G*bwd fused W=%d block=%d grid=%d smem=%d", an[plan->conv_axis],
+                 L.args.W, L.block, L.grid, L.smem);
+        s += tmp;
+    } else {
+        s += " | convolve: forward, multiply, backward";
+    }
     }
     if (buf && cap > 0) {
         size_t m = s.size() < (size_t)(cap - 1) ? s.size() : (size_t)(cap - 1);
@@ -554,7 +605,8 @@ int croft_plan_num_launches(croft_plan plan) {
 
 croft_status croft_plan_set_timing(croft_plan plan, int enable) {
     if (!plan) return CROFT_ERR_INVALID_ARG;
-    const size_t need = (size_t)(plan->batch ? 2 : plan->ngroups + 1);
+    // (a convolution records up to 2 * ngroups + 1 logical passes)
+    const size_t need = (size_t)(plan->batch ? 2 : 2 * plan->ngroups + 2);
     if (enable && plan->ev.size() < need) {
         while (plan->ev.size() < need) {
             cudaEvent_t e;
@@ -593,14 +645,42 @@ croft_status croft_plan_last_device_status(croft_plan plan) {
     return CROFT_OK;
 }
 
+// Launches passes [i0, i1) with the given sign.  A pass marked src_in reads `in`
+// unless force_out (every pass after the first logical one reads `out`).  With
+// evi, records the next timing event at the end of every logical pass.
+static croft_status run_passes(croft_plan plan, size_t i0, size_t i1, const void* in, void* out, cudaStream_t s,
+                               float isign, bool force_out, int* evi) {
+    for (size_t i = i0; i < i1; ++i) {
+        PassLaunch L = plan->passes[i];
+        L.args.isign = isign;
+        L.pargs.isign = isign;
+        const size_t es = L.f64 ? sizeof(double2) : sizeof(float2);
+        const char* src = ((L.src_in && !force_out) ? (const char*)in : (const char*)out) + (size_t)L.offset * es;
+        char* dst = (char*)out + (size_t)L.offset * es;
+        if (launch_pass(L, src, dst, s) != cudaSuccess) { cudaGetLastError(); return CROFT_ERR_CUDA; }
+        const bool group_end = (i + 1 == i1) || plan->passes[i + 1].group != L.group;
+        if (evi && group_end && cudaEventRecord(plan->ev[(*evi)++], s) != cudaSuccess) {
+            cudaGetLastError();
+            return CROFT_ERR_CUDA;
+        }
+    }
+    return CROFT_OK;
+}
+
+static size_t elem_bytes(const croft_plan plan) { return plan->dtype == CROFT_C2C_F64 ? sizeof(double2) : sizeof(float2); }
+
+static bool overlaps(const void* a, size_t na, const void* b, size_t nb) {
+    const char* x = (const char*)a;
+    const char* y = (const char*)b;
+    return x < y + nb && y < x + na;
+}
+
 static croft_status exec_dir(croft_plan plan, const void* in, void* out, void* stream, float isign) {
     if (!plan || !in || !out || plan->batch) return CROFT_ERR_INVALID_ARG;
     if (((uintptr_t)in & 15) || ((uintptr_t)out & 15)) return CROFT_ERR_INVALID_ARG;
     const long long N = (long long)plan->dims[0] * plan->dims[1] * plan->dims[2];
-    const size_t bytes = (size_t)N * (plan->dtype == CROFT_C2C_F64 ? sizeof(double2) : sizeof(float2));
-    const char* a = (const char*)in;
-    const char* b = (const char*)out;
-    if (a != b && a < b + bytes && b < a + bytes) return CROFT_ERR_INVALID_ARG;
+    const size_t bytes = (size_t)N * elem_bytes(plan);
+    if (in != out && overlaps(in, bytes, out, bytes)) return CROFT_ERR_INVALID_ARG;
     cudaStream_t s = (cudaStream_t)stream;
     if (plan->passes.empty()) {
         if (in != out && cudaMemcpyAsync(out, in, bytes, cudaMemcpyDeviceToDevice, s) != cudaSuccess) {
@@ -615,23 +695,63 @@ static croft_status exec_dir(croft_plan plan, const void* in, void* out, void* s
         cudaGetLastError();
         return CROFT_ERR_CUDA;
     }
-    if (tm && cudaEventRecord(plan->ev[0], s) != cudaSuccess) { cudaGetLastError(); return CROFT_ERR_CUDA; }
-    for (size_t i = 0; i < plan->passes.size(); ++i) {
-        PassLaunch L = plan->passes[i];
-        L.args.isign = isign;
-        L.pargs.isign = isign;
-        const size_t es = L.f64 ? sizeof(double2) : sizeof(float2);
-        const char* src = (L.src_in ? (const char*)in : (const char*)out) + (size_t)L.offset * es;
-        char* dst = (char*)out + (size_t)L.offset * es;
-        cudaError_t e = launch_pass(L, src, dst, s);
-        if (e != cudaSuccess) { cudaGetLastError(); return CROFT_ERR_CUDA; }
-        const bool group_end = (i + 1 == plan->passes.size()) || plan->passes[i + 1].group != L.group;
-        if (tm && group_end && cudaEventRecord(plan->ev[L.group + 1], s) != cudaSuccess) {
+    int evi = 0;
+    if (tm) {
+        if (cudaEventRecord(plan->ev[0], s) != cudaSuccess) { cudaGetLastError(); return CROFT_ERR_CUDA; }
+        evi = 1;
+    }
+    croft_status st = run_passes(plan, 0, plan->passes.size(), in, out, s, isign, false, tm ? &evi : nullptr);
+    if (st != CROFT_OK) return st;
+    plan->ev_count = tm ? evi : 0;
+    plan->ran = true;
+    return CROFT_OK;
+}
+
+croft_status croft_exec_convolve(croft_plan plan, const void* in, void* out, const void* g, void* stream) {
+    if (!plan || !in || !out || !g || plan->batch) return CROFT_ERR_INVALID_ARG;
+    const bool f64 = plan->dtype == CROFT_C2C_F64;
+    const size_t rs = f64 ? sizeof(double) : sizeof(float);
+    if (((uintptr_t)in & 15) || ((uintptr_t)out & 15) || ((uintptr_t)g & (rs - 1))) return CROFT_ERR_INVALID_ARG;
+    const long long N = (long long)plan->dims[0] * plan->dims[1] * plan->dims[2];
+    const size_t bytes = (size_t)N * elem_bytes(plan);
+    if (in != out && overlaps(in, bytes, out, bytes)) return CROFT_ERR_INVALID_ARG;
+    if (overlaps(g, (size_t)N * rs, out, bytes)) return CROFT_ERR_INVALID_ARG;
+    cudaStream_t s = (cudaStream_t)stream;
+    const bool tm = plan->timing;
+    if (plan->d_status && cudaMemsetAsync(plan->d_status, 0, sizeof(int), s) != cudaSuccess) {
+        cudaGetLastError();
+        return CROFT_ERR_CUDA;
+    }
+    int evi = 0;
+    int* pe = tm ? &evi : nullptr;
+    if (tm) {
+        if (cudaEventRecord(plan->ev[0], s) != cudaSuccess) { cudaGetLastError(); return CROFT_ERR_CUDA; }
+        evi = 1;
+    }
+    croft_status st = CROFT_OK;
+    if (plan->conv_fused) {
+        // forward passes but the last, the fused last-axis pass, backward passes of the other axes
+        const size_t last = plan->passes.size() - 1;
+        st = run_passes(plan, 0, last, in, out, s, 1.0f, false, pe);
+        if (st != CROFT_OK) return st;
+        const PassLaunch& L = plan->conv;
+        if (launch_conv(L, L.src_in ? in : out, out, g, s) != cudaSuccess) { cudaGetLastError(); return CROFT_ERR_CUDA; }
+        if (tm && cudaEventRecord(plan->ev[evi++], s) != cudaSuccess) { cudaGetLastError(); return CROFT_ERR_CUDA; }
+        st = run_passes(plan, 0, last, in, out, s, -1.0f, true, pe);
+        if (st != CROFT_OK) return st;
+    } else {
+        // F, multiply, B (a one-point grid has no passes: the multiply reads `in`)
+        st = run_passes(plan, 0, plan->passes.size(), in, out, s, 1.0f, false, pe);
+        if (st != CROFT_OK) return st;
+        if (launch_scale(plan->passes.empty() ? in : out, out, g, N, f64, s) != cudaSuccess) {
             cudaGetLastError();
             return CROFT_ERR_CUDA;
         }
+        if (tm && cudaEventRecord(plan->ev[evi++], s) != cudaSuccess) { cudaGetLastError(); return CROFT_ERR_CUDA; }
+        st = run_passes(plan, 0, plan->passes.size(), in, out, s, -1.0f, true, pe);
+        if (st != CROFT_OK) return st;
     }
-    plan->ev_count = tm ? plan->ngroups + 1 : 0;
+    plan->ev_count = tm ? evi : 0;
     plan->ran = true;
     return CROFT_OK;
 }

@@ -17,3 +17,8 @@
 #define CROFT_SIZES_3(X) X(5) X(10) X(18) X(27) X(40) X(54) X(75) X(96) X(125) X(150) X(192) X(240) X(270) \
     X(324) X(400) X(480) X(540) X(640) X(729) X(810) X(972) X(1125) X(1250) X(1440) X(1600) X(1875) X(2025) \
     X(2250) X(2500) X(2880) X(3125) X(3456) X(3840) X(4096)
+
+// complex128 lengths (croft_kernels64.cu, croft_conv.cu): every power of two up to
+// 1024 and a few mixed-radix ones.
+#define CROFT_SIZES64(X) \
+    X(2) X(3) X(4) X(5) X(6) X(8) X(10) X(12) X(15) X(16) X(32) X(48) X(60) X(64) X(96) X(120) X(128) X(256) X(512) X(1024)
