@@ -217,26 +217,38 @@ def _flush(flush):
 
 
 def time_transform(croft, torch, stream, flush, plan, run_fwd, run_bwd, reps=5, warm=2):  # noqa: PLR0913
-    """Median device ms of forward and backward (L2 flushed before each) and mean per-pass ms."""
-    fw, bw, passes = [], [], []
+    """Median device ms of forward and backward (L2 flushed before each, no events between the passes),
+    then the mean per-pass ms from `reps` further runs with per-pass events.  (An event recorded
+    between two passes stops the next pass from launching early, so the whole-transform times
+    are taken without them.)"""
+    def once(fn, per_pass):
+        with torch.cuda.stream(stream):
+            _flush(flush)
+            a = torch.cuda.Event(enable_timing=True)
+            b = torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            fn()
+            b.record(stream)
+        pt = croft.croft_plan_pass_times(plan) if per_pass else []
+        stream.synchronize()
+        return a.elapsed_time(b), pt
+
+    if plan:
+        croft.croft_plan_set_timing(plan, False)
+    fw, bw = [], []
     for i in range(warm + reps):
-        res = []
-        for fn in (run_fwd, run_bwd):
-            with torch.cuda.stream(stream):
-                _flush(flush)
-                a = torch.cuda.Event(enable_timing=True)
-                b = torch.cuda.Event(enable_timing=True)
-                a.record(stream)
-                fn()
-                b.record(stream)
-            pt = croft.croft_plan_pass_times(plan) if plan else []
-            stream.synchronize()
-            res.append((a.elapsed_time(b), pt))
+        tf, _ = once(run_fwd, False)
+        tb, _ = once(run_bwd, False)
         if i >= warm:
-            fw.append(res[0][0])
-            bw.append(res[1][0])
-            passes.append(res[0][1])
-            passes.append(res[1][1])
+            fw.append(tf)
+            bw.append(tb)
+    passes = []
+    if plan:
+        croft.croft_plan_set_timing(plan, True)
+        for _ in range(reps):
+            passes.append(once(run_fwd, True)[1])
+            passes.append(once(run_bwd, True)[1])
+        croft.croft_plan_set_timing(plan, False)
     np_ = len(passes[0]) if passes and passes[0] else 0
     pass_ms = [statistics.mean(p[i] for p in passes) for i in range(np_)]
     return statistics.median(fw), statistics.median(bw), pass_ms
@@ -292,10 +304,11 @@ def measure_rows(croft, torch, dev, stream, flush, peak):
     y2 = torch.empty_like(x)
     g = torch.from_numpy(S.pme_influence(shape)).to(dev)
     with croft.Plan(*shape) as p:
-        croft.croft_plan_set_timing(p.handle, True)
         sh = stream.cuda_stream
         t_conv, t_sep, pts = [], [], []
-        for i in range(2 + 5):
+        for i in range(2 + 5 + 5):
+            per_pass = i >= 7  # the last runs: per-pass events (kept out of the whole-pipeline times)
+            croft.croft_plan_set_timing(p.handle, per_pass)
             for kind in ("conv", "sep"):
                 with torch.cuda.stream(stream):
                     _flush(flush)
@@ -309,12 +322,12 @@ def measure_rows(croft, torch, dev, stream, flush, peak):
                         y2.mul_(g)
                         croft.croft_exec_backward(p.handle, y2, y2, sh)
                     b.record(stream)
-                pt = croft.croft_plan_pass_times(p.handle, 16) if kind == "conv" else None
+                pt = croft.croft_plan_pass_times(p.handle, 16) if (kind == "conv" and per_pass) else None
                 stream.synchronize()
-                if i >= 2:
+                if 2 <= i < 7:
                     (t_conv if kind == "conv" else t_sep).append(a.elapsed_time(b))
-                    if pt:
-                        pts.append(pt)
+                if pt:
+                    pts.append(pt)
         desc = p.describe()
     stream.synchronize()
     diff = float(torch.linalg.vector_norm((y - y2).flatten()) / torch.linalg.vector_norm(y2.flatten()))
@@ -422,29 +435,36 @@ def run_croft(args):
              "plane_fused": croft.CROFT_SCHEDULE_PLANE_FUSED, "slab_l2": croft.CROFT_SCHEDULE_SLAB_L2}[args.schedule]
     plan = croft.Plan(*shape, schedule=sched)
     plan_desc = plan.describe()
-    croft.croft_plan_set_timing(plan.handle, True)
     launches_per_step = 2 * croft.croft_plan_num_launches(plan.handle)
     sh = stream.cuda_stream
 
     gap_fills = [1]
 
     def step(record):
+        """One forward + backward; device time between two events (none between the passes)."""
         with torch.cuda.stream(stream):
             for _ in range(gap_fills[0]):
                 flush.fill_(1.0)
-            e = [torch.cuda.Event(enable_timing=True) for _ in range(4)]
+            e = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
             e[0].record(stream)
             croft.croft_exec_forward(plan.handle, x, y, sh)
-            e[1].record(stream)
-        pf = croft.croft_plan_pass_times(plan.handle)
-        with torch.cuda.stream(stream):
-            e[2].record(stream)
             croft.croft_exec_backward(plan.handle, y, z, sh)
-            e[3].record(stream)
-        pb = croft.croft_plan_pass_times(plan.handle)
+            e[1].record(stream)
         stream.synchronize()
         if record is not None:
-            record.append((e[0].elapsed_time(e[1]) + e[2].elapsed_time(e[3]), pf, pb))
+            record.append(e[0].elapsed_time(e[1]))
+
+    def step_per_pass(record):
+        """The same step with an event after every pass (per-kernel durations)."""
+        with torch.cuda.stream(stream):
+            flush.fill_(1.0)
+            croft.croft_exec_forward(plan.handle, x, y, sh)
+        pf = croft.croft_plan_pass_times(plan.handle)
+        with torch.cuda.stream(stream):
+            croft.croft_exec_backward(plan.handle, y, z, sh)
+        pb = croft.croft_plan_pass_times(plan.handle)
+        stream.synchronize()
+        record.append((pf, pb))
 
     for _ in range(args.warmup):
         step(None)
@@ -472,8 +492,14 @@ def run_croft(args):
         step(rec)
     torch.cuda.synchronize()
     t_wall = time.perf_counter() - t_wall
+    # per-kernel durations: the same steps again with per-pass events, right after the timed ones
+    croft.croft_plan_set_timing(plan.handle, True)
+    rec_pp = []
+    for _ in range(args.steps):
+        step_per_pass(rec_pp)
+    croft.croft_plan_set_timing(plan.handle, False)
     clk = clocks.stop()
-    ms_total = sum(r[0] for r in rec)
+    ms_total = sum(rec)
     if world > 1:
         t = torch.tensor([ms_total], device=dev)
         torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
@@ -483,8 +509,8 @@ def run_croft(args):
     value = world * flops_step / (ms_step * 1e-3) / 1e9
 
     # per-pass kernel times (forward and backward run the same kernels)
-    npass = len(rec[0][1])
-    pass_ms = [statistics.mean([r[1][i] for r in rec] + [r[2][i] for r in rec]) for i in range(npass)]
+    npass = len(rec_pp[0][0])
+    pass_ms = [statistics.mean([r[0][i] for r in rec_pp] + [r[1][i] for r in rec_pp]) for i in range(npass)]
     dom = max(range(npass), key=lambda i: pass_ms[i])
     axis_names = {3: ["z", "y", "x"], 2: ["yz", "x"], 1: ["yz"]}.get(npass, [f"p{i}" for i in range(npass)])
     peak, peak_kind = measured_peaks()
@@ -568,7 +594,12 @@ def run_croft(args):
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                          "frac": achieved / peak, "traffic": traffic, "kernel": dom_key,
                          "peak_source": peak_kind, "alg_bytes_per_launch": alg_bytes,
-                         "pass_ms": pass_ms},
+                         "pass_ms": pass_ms,
+                         "kernel_timing": "CUDA events on the launch stream after every pass, over "
+                                          f"{args.steps} forward+backward steps run right after the timed "
+                                          "ones (an event between two passes stops the next pass from "
+                                          "launching early, so the timed steps carry events only at "
+                                          "their ends)"},
             "hbm_frac_whole_transform": (16.0 * n_total * 2 / (ms_step * 1e-3) / 1e9) / peak,
             "cpu_baseline": cpu,
             "e2e": {"value": e2e_val, "unit": "GFLOP/s", "h2d_bytes_per_step": 8 * n_total,

@@ -35,15 +35,24 @@ conv64_fn conv64_kernel_for(int n) {
 #undef CROFT_CONV64_CASE
 }
 
-cudaError_t launch_scale(const void* in, void* out, const void* g, long long n, bool f64, cudaStream_t s) {
+cudaError_t launch_scale(const void* in, void* out, const void* g, long long n, bool f64, cudaStream_t s, bool pdl) {
     if (n <= 0) return cudaSuccess;
     long long blocks = (n + 255) / 256;
     if (blocks > 152LL * 8) blocks = 152LL * 8;
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3((unsigned)blocks, 1, 1);
+    cfg.blockDim = dim3(256, 1, 1);
+    cfg.stream = s;
+    cudaLaunchAttribute attr[1];
+    if (pdl) {
+        attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+        attr[0].val.programmaticStreamSerializationAllowed = 1;
+        cfg.attrs = attr;
+        cfg.numAttrs = 1;
+    }
     if (f64)
-        croft_scale_kernel<double2><<<(int)blocks, 256, 0, s>>>((const double2*)in, (double2*)out, (const double*)g, n);
-    else
-        croft_scale_kernel<float2><<<(int)blocks, 256, 0, s>>>((const float2*)in, (float2*)out, (const float*)g, n);
-    return cudaGetLastError();
+        return cudaLaunchKernelEx(&cfg, croft_scale_kernel<double2>, (const double2*)in, (double2*)out, (const double*)g, n);
+    return cudaLaunchKernelEx(&cfg, croft_scale_kernel<float2>, (const float2*)in, (float2*)out, (const float*)g, n);
 }
 #endif
 

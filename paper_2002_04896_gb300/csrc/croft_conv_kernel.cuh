@@ -12,7 +12,8 @@
 // grid (the forward pass's write and the backward pass's read) and the
 // separate multiply pass; the other axes run as ordinary passes.
 //
-// Tile: W adjacent columns of the axis (COL layout, croft_internal.h), the
+// Tile: W adjacent columns of the axis (COL layout, croft_internal.h; W fixed per
+// length by croft_conv_width), the
 // matching W columns of G (real, same layout as the grid) and the twiddles.
 // G is copied to shared memory with cp.async at the start, so its latency
 // hides behind the forward stages.  The backward transform is conj(F(conj(.))):
@@ -25,13 +26,12 @@
 namespace croft {
 
 // Store of the last forward stage: element a of this column times G(a), conjugated.
-template <class C>
+template <class C, int W>
 struct ScaleConjCol {
     using value_type = C;
     using R = typename CxScalar<C>::T;
     C* s;        // tile + c
     const R* g;  // G tile + c
-    int W;
     __device__ __forceinline__ void store(int a, C v) const {
         const R ga = g[a * W];
         s[a * W] = mkc<C>(v.x * ga, -(v.y * ga));
@@ -47,38 +47,57 @@ __device__ __forceinline__ void conv_cp_async(R* dst_smem, const R* src) {
         asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"(d), "l"(src) : "memory");
 }
 
+// Launch shape: W = croft_conv_width(N) columns of T threads (a compile-time
+// constant, so every shared-memory index folds into constants).  For complex64
+// power-of-two lengths with 16-thread pencils (W = 16, 256-thread CTAs), asking
+// for four CTAs per SM keeps the kernel at 64 registers (72 at N = 256
+// otherwise: three CTAs per SM).  Other lengths keep the 128-register bound:
+// radix-3/5 stages and complex128 spill at 64, and 32-thread pencils measured
+// slower with four 64-register CTAs than with three (512^3: 1006 vs 944 us).
+template <int N, class C>
+struct ConvShape {
+    static constexpr int T = croft_threads_per_pencil(N);
+    static constexpr int W = croft_conv_width(N, (int)sizeof(C));
+    static constexpr int THREADS = W * T;
+    static constexpr bool TIGHT = sizeof(C) == 8 && THREADS == 256 && T <= 16 && (N & (N - 1)) == 0;
+    static constexpr int MIN_BLOCKS = TIGHT ? 4 : (THREADS <= 256 ? 2 : 1);
+};
+
 // Shared memory: [twiddles: tw_pad][tile: N x W complex][G tile: N x W real].
 template <int N, class C = float2>
-__global__ void __launch_bounds__(512) croft_conv_kernel(const C* in, C* out, const typename CxScalar<C>::T* g,
-                                                         const __grid_constant__ PassArgs A) {
+__global__ void __launch_bounds__(ConvShape<N, C>::THREADS, ConvShape<N, C>::MIN_BLOCKS)
+    croft_conv_kernel(const C* in, C* out, const typename CxScalar<C>::T* g, const __grid_constant__ PassArgs A) {
     using R = typename CxScalar<C>::T;
-    constexpr int T = croft_threads_per_pencil(N);
+    constexpr int T = ConvShape<N, C>::T;
+    constexpr int W = ConvShape<N, C>::W;
     constexpr CroftSched sc = croft_make_sched(N);
     extern __shared__ __align__(16) unsigned char smem_raw[];
     C* stw = reinterpret_cast<C*>(smem_raw);
     C* tile = stw + A.tw_pad;
-    R* gtile = reinterpret_cast<R*>(tile + (long long)N * A.W);
+    R* gtile = reinterpret_cast<R*>(tile + (long long)N * W);
     const C* twg;
     if constexpr (sizeof(C) == 16) twg = A.tw64;
     else twg = A.tw;
 
-    const int c = threadIdx.x % A.W;
-    const int lane = threadIdx.x / A.W;
-    const long long col = (long long)blockIdx.x * A.W + c;
+    const int c = threadIdx.x % W;
+    const int lane = threadIdx.x / W;
+    const long long col = (long long)blockIdx.x * W + c;
     const bool ok = col < A.ncols;
     const long long b = col / A.M;
     const long long m = col - b * A.M;
     const long long base = b * (long long)N * A.M + m;
 
+    pdl_allow_dependents();
     if (ok)
-        for (int a = lane; a < N; a += T) conv_cp_async(gtile + a * A.W + c, g + base + (long long)a * A.M);
+        for (int a = lane; a < N; a += T) conv_cp_async(gtile + a * W + c, g + base + (long long)a * A.M);
     asm volatile("cp.async.commit_group;" ::: "memory");
     if (sc.count > 1)
         for (int i = threadIdx.x; i < N - 1; i += blockDim.x) stw[i] = twg[i];
+    pdl_wait();  // (G and the twiddles are not written by the previous pass)
 
     const GlobalInT<C> src{in + base, A.M, 1.f};
-    const SmemColT<C> work{tile + c, A.W};
-    const ScaleConjCol<C> scaled{tile + c, gtile + c, A.W};
+    const SmemColFixed<C, W> work{tile + c};
+    const ScaleConjCol<C, W> scaled{tile + c, gtile + c};
     const GlobalOutT<C> dst{out + base, A.M, -1.f};
 
     // forward transform of the column; its last stage leaves conj(G * Y) in the tile.
@@ -110,6 +129,8 @@ __global__ void __launch_bounds__(512) croft_conv_kernel(const C* in, C* out, co
 // tensor-core pass).  Grid-stride loop.
 template <class C>
 __global__ void croft_scale_kernel(const C* in, C* out, const typename CxScalar<C>::T* g, long long n) {
+    pdl_allow_dependents();
+    pdl_wait();
     for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
         const C v = in[i];
         const typename CxScalar<C>::T s = g[i];

@@ -118,6 +118,26 @@ struct SmemColT {
     __device__ __forceinline__ void store(int a, C v) const { s[a * W] = v; }
 };
 using SmemCol = SmemColT<float2>;
+// The same with a compile-time width (the index arithmetic folds into constants).
+template <class C, int W>
+struct SmemColFixed {
+    using value_type = C;
+    C* s;  // tile + c
+    __device__ __forceinline__ C load(int a) const { return s[a * W]; }
+    __device__ __forceinline__ void store(int a, C v) const { s[a * W] = v; }
+};
+
+// ---------------------------------------------------------------------------
+// programmatic dependent launch
+// ---------------------------------------------------------------------------
+// Passes after the first of an exec are launched with programmatic stream
+// serialisation: their CTAs may become resident while the previous pass drains.
+// Every such kernel loads what the previous pass does not write (twiddles, the
+// influence function), then waits here for the previous grid to complete and its
+// writes to become visible, before it reads the grid.  Without the launch
+// attribute both instructions return at once.
+__device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+__device__ __forceinline__ void pdl_allow_dependents() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
 
 // ---------------------------------------------------------------------------
 // barriers

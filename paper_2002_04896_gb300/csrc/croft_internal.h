@@ -120,7 +120,8 @@ conv_fn lookup_conv_kernel_group_2(int n);
 conv_fn lookup_conv_kernel_group_3(int n);
 conv64_fn conv64_kernel_for(int n);
 // out = in * g elementwise (complex times real), n elements
-cudaError_t launch_scale(const void* in, void* out, const void* g, long long n, bool f64, cudaStream_t s);
+cudaError_t launch_scale(const void* in, void* out, const void* g, long long n, bool f64, cudaStream_t s,
+                         bool pdl = false);
 
 // croft_passes.cu
 pass_fn pass_kernel_for(int layout, int n);
@@ -128,9 +129,11 @@ conv_fn conv_kernel_for(int n);
 pipe_fn pipe_kernel_for(int layout, int n);
 int pipe_blocks_per_sm(const PassLaunch& L);
 cudaError_t prepare_pass(const PassLaunch& L);  // once per plan: shared-memory / cluster opt-ins, occupancy check
-cudaError_t launch_pass(const PassLaunch& L, const void* in, void* out, cudaStream_t s);
+// pdl: launch with programmatic stream serialisation (ignored for kernels that do not wait for it)
+cudaError_t launch_pass(const PassLaunch& L, const void* in, void* out, cudaStream_t s, bool pdl = false);
+bool pass_supports_pdl(const PassLaunch& L);
 // the fused convolution pass (args/shape of a COL pass; g: the real influence function)
-cudaError_t launch_conv(const PassLaunch& L, const void* in, void* out, const void* g, cudaStream_t s);
+cudaError_t launch_conv(const PassLaunch& L, const void* in, void* out, const void* g, cudaStream_t s, bool pdl = false);
 int active_clusters(const PassLaunch& L);  // co-resident clusters of a plane pass (0 for axis passes)
 
 }  // namespace croft

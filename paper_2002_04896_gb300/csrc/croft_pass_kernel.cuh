@@ -37,8 +37,10 @@ __global__ void __launch_bounds__(512) croft_pass_kernel(const C* in, C* out, co
     const C* twg;
     if constexpr (sizeof(C) == 16) twg = A.tw64;
     else twg = A.tw;
+    pdl_allow_dependents();
     if (croft_make_sched(N).count > 1)
         for (int i = threadIdx.x; i < N - 1; i += blockDim.x) stw[i] = twg[i];
+    pdl_wait();
 
     if (LAYOUT == LAYOUT_ROW) {
         const int c = threadIdx.x / T;

@@ -74,7 +74,8 @@ conv_fn conv_kernel_for(int n) {
     return f;
 }
 
-static cudaLaunchConfig_t plane_config(const PassLaunch& L, cudaStream_t s, cudaLaunchAttribute* attr) {
+// attr must have room for two entries: the cluster shape and, with pdl, programmatic serialisation.
+static cudaLaunchConfig_t plane_config(const PassLaunch& L, cudaStream_t s, cudaLaunchAttribute* attr, bool pdl = false) {
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3((unsigned)L.grid, 1, 1);
     cfg.blockDim = dim3((unsigned)L.block, 1, 1);
@@ -86,8 +87,34 @@ static cudaLaunchConfig_t plane_config(const PassLaunch& L, cudaStream_t s, cuda
     attr[0].val.clusterDim.z = 1;
     cfg.attrs = attr;
     cfg.numAttrs = 1;
+    if (pdl) {
+        attr[1].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+        attr[1].val.programmaticStreamSerializationAllowed = 1;
+        cfg.numAttrs = 2;
+    }
     return cfg;
 }
+
+// Plain launch of a pass-shaped kernel, with programmatic stream serialisation when pdl
+// (the kernel must call pdl_wait() before reading what the previous launch wrote).
+template <class... P, class... A>
+static cudaError_t launch_ex(void (*f)(P...), const PassLaunch& L, cudaStream_t s, bool pdl, A... args) {
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3((unsigned)L.grid, 1, 1);
+    cfg.blockDim = dim3((unsigned)L.block, 1, 1);
+    cfg.dynamicSmemBytes = (size_t)L.smem;
+    cfg.stream = s;
+    cudaLaunchAttribute attr[1];
+    if (pdl) {
+        attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+        attr[0].val.programmaticStreamSerializationAllowed = 1;
+        cfg.attrs = attr;
+        cfg.numAttrs = 1;
+    }
+    return cudaLaunchKernelEx(&cfg, f, args...);
+}
+
+bool pass_supports_pdl(const PassLaunch& L) { return !L.tc && !L.pipe; }
 
 cudaError_t prepare_pass(const PassLaunch& L) {
     if (L.kind == PASS_PLANE) {
@@ -98,7 +125,7 @@ cudaError_t prepare_pass(const PassLaunch& L) {
             if (e != cudaSuccess) return e;
         }
         // the cluster must fit on the device at all
-        cudaLaunchAttribute attr[1];
+        cudaLaunchAttribute attr[2];
         cudaLaunchConfig_t cfg = plane_config(L, 0, attr);
         int nclusters = 0;
         e = cudaOccupancyMaxActiveClusters(&nclusters, L.pk.fn, &cfg);
@@ -123,18 +150,18 @@ cudaError_t prepare_pass(const PassLaunch& L) {
     return cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, L.smem);
 }
 
-cudaError_t launch_pass(const PassLaunch& L, const void* vin, void* vout, cudaStream_t s) {
+cudaError_t launch_pass(const PassLaunch& L, const void* vin, void* vout, cudaStream_t s, bool pdl) {
+    pdl = pdl && pass_supports_pdl(L);
     if (L.f64) {
         pass64_fn f = pass64_kernel_for(L.layout, L.args.n);
         if (!f) return cudaErrorInvalidValue;
-        f<<<L.grid, L.block, L.smem, s>>>((const double2*)vin, (double2*)vout, L.args);
-        return cudaGetLastError();
+        return launch_ex(f, L, s, pdl, (const double2*)vin, (double2*)vout, L.args);
     }
     const float2* in = (const float2*)vin;
     float2* out = (float2*)vout;
     if (L.kind == PASS_PLANE) {
-        cudaLaunchAttribute attr[1];
-        cudaLaunchConfig_t cfg = plane_config(L, s, attr);
+        cudaLaunchAttribute attr[2];
+        cudaLaunchConfig_t cfg = plane_config(L, s, attr, pdl);
         return cudaLaunchKernelEx(&cfg, L.pk.fn, in, out, L.pargs);
     }
     if (L.pipe) {
@@ -148,28 +175,31 @@ cudaError_t launch_pass(const PassLaunch& L, const void* vin, void* vout, cudaSt
         f<<<L.grid, L.block, L.smem, s>>>(in, out, pa, map);
         return cudaGetLastError();
     }
-    pass_fn f = L.tc ? tc_pass_kernel_for(L.layout, L.args.n) : pass_kernel_for(L.layout, L.args.n);
+    if (L.tc) {
+        pass_fn f = tc_pass_kernel_for(L.layout, L.args.n);
+        if (!f) return cudaErrorInvalidValue;
+        f<<<L.grid, L.block, L.smem, s>>>(in, out, L.args);
+        return cudaGetLastError();
+    }
+    pass_fn f = pass_kernel_for(L.layout, L.args.n);
     if (!f) return cudaErrorInvalidValue;
-    f<<<L.grid, L.block, L.smem, s>>>(in, out, L.args);
-    return cudaGetLastError();
+    return launch_ex(f, L, s, pdl, in, out, L.args);
 }
 
-cudaError_t launch_conv(const PassLaunch& L, const void* in, void* out, const void* g, cudaStream_t s) {
+cudaError_t launch_conv(const PassLaunch& L, const void* in, void* out, const void* g, cudaStream_t s, bool pdl) {
     if (L.f64) {
         conv64_fn f = conv64_kernel_for(L.args.n);
         if (!f) return cudaErrorInvalidValue;
-        f<<<L.grid, L.block, L.smem, s>>>((const double2*)in, (double2*)out, (const double*)g, L.args);
-    } else {
-        conv_fn f = conv_kernel_for(L.args.n);
-        if (!f) return cudaErrorInvalidValue;
-        f<<<L.grid, L.block, L.smem, s>>>((const float2*)in, (float2*)out, (const float*)g, L.args);
+        return launch_ex(f, L, s, pdl, (const double2*)in, (double2*)out, (const double*)g, L.args);
     }
-    return cudaGetLastError();
+    conv_fn f = conv_kernel_for(L.args.n);
+    if (!f) return cudaErrorInvalidValue;
+    return launch_ex(f, L, s, pdl, (const float2*)in, (float2*)out, (const float*)g, L.args);
 }
 
 int active_clusters(const PassLaunch& L) {
     if (L.kind != PASS_PLANE) return 0;
-    cudaLaunchAttribute attr[1];
+    cudaLaunchAttribute attr[2];
     cudaLaunchConfig_t cfg = plane_config(L, 0, attr);
     int n = 0;
     if (cudaOccupancyMaxActiveClusters(&n, L.pk.fn, &cfg) != cudaSuccess) {

@@ -115,13 +115,23 @@ std::string batch_describe(const croft_plan_s* p);
 
 static int g_max_smem = 0;
 
+// Tuning override of the column-tile width: the first of the named variables that is set (0: none).
+static int env_width(const char* a, const char* b = nullptr) {
+    for (const char* k : {a, b}) {
+        if (!k) continue;
+        const char* v = getenv(k);
+        if (v && atoi(v) >= 1) return atoi(v);
+    }
+    return 0;
+}
+
 // Launch shape of one pass (layouts: croft_internal.h; kernel: croft_pass_kernel.cuh).
 // ROW: W pencils of length n per CTA, each padded to n + n/16 + 1 slots.
 // COL: W adjacent columns per CTA, W a multiple of 16 (128-byte rows).
 // Aim for ~256 threads per CTA and <= 100 KB of shared memory so that at
 // least two CTAs share an SM.
 static bool shape_pass(PassLaunch& L, int layout, int n, long long M, long long ncols, bool tc = false,
-                       bool f64 = false) {
+                       bool f64 = false, int want_w = 0) {
     memset(&L, 0, sizeof(L));
     L.layout = layout;
     L.tc = tc ? 1 : 0;
@@ -147,8 +157,13 @@ static bool shape_pass(PassLaunch& L, int layout, int n, long long M, long long 
     } else {
         int W = 16;
         while (W * 2 * T <= 256) W *= 2;
-        const char* cw = getenv("CROFT_COL_W");  // tuning override of the column-tile width
-        if (cw && atoi(cw) >= 1 && !tc) W = atoi(cw);
+        // Pencils of 32 threads (lengths of a few hundred): 16 columns make 512-thread CTAs,
+        // two per SM (registers).  Where the rows of a pencil are close (axis stride up to
+        // 64 KB) 8 columns - 256-thread CTAs, four per SM - measured faster (y pass of 480^3:
+        // 457 -> 409 us); across long strides (the x pass) the 64-byte row segments cost more
+        // than the occupancy gains (480^3: 463 -> 514 us), so 16 stays.
+        if (!tc && !f64 && T == 32 && M * es <= 64 * 1024) W = 8;
+        if (want_w >= 1 && !tc) W = want_w;
         while (W > 1 && (W * T > max_threads || (A.tw_pad + (long long)n * W) * es > smem_cap)) W /= 2;
         A.W = W;
         L.smem = (int)((A.tw_pad + (long long)n * W) * es);
@@ -299,7 +314,8 @@ static croft_status add_axis_pass(croft_plan p, int axis, int x0 = 0, int nxs = 
         }
     }
     PassLaunch L;
-    if (!shape_pass(L, layout, n, M, N / n, p->axis_tc[axis], f64)) return CROFT_ERR_UNSUPPORTED_SIZE;
+    const int want_w = layout == LAYOUT_COL ? env_width(axis == 1 ? "CROFT_COL_W_Y" : "CROFT_COL_W_X", "CROFT_COL_W") : 0;
+    if (!shape_pass(L, layout, n, M, N / n, p->axis_tc[axis], f64, want_w)) return CROFT_ERR_UNSUPPORTED_SIZE;
     L.kind = PASS_AXIS;
     L.args.tw = p->tw_dev[axis];
     L.args.tw64 = f64 ? (const double2*)p->tw_dev[axis] : nullptr;
@@ -377,7 +393,11 @@ static void plan_conv(croft_plan p) {
     const long long M = (axis == 2) ? 1 : (axis == 1 ? (long long)p->dims[2] : (long long)p->dims[1] * p->dims[2]);
     if (f64 ? !conv64_kernel_for(n) : !conv_kernel_for(n)) return;
     PassLaunch L;
-    if (!shape_pass(L, LAYOUT_COL, n, M, N / n, false, f64)) return;
+    // the kernel's column width is a compile-time constant (croft_conv_width): for 32-thread
+    // pencils 8 columns whatever the stride - the fused pass does twice the arithmetic per
+    // byte, so occupancy matters more (480^3: 927 -> 801 us)
+    const int want_w = croft_conv_width(n, f64 ? 16 : 8);
+    if (!shape_pass(L, LAYOUT_COL, n, M, N / n, false, f64, want_w) || L.args.W != want_w) return;
     const long long es = f64 ? 16 : 8;
     const long long smem = ((long long)L.args.tw_pad + (long long)n * L.args.W) * es + (long long)n * L.args.W * (es / 2);
     if (smem > g_max_smem) return;
@@ -389,6 +409,11 @@ static void plan_conv(croft_plan p) {
     L.group = Lp.group;
     L.src_in = Lp.src_in;
     const void* fn = f64 ? (const void*)conv64_kernel_for(n) : (const void*)conv_kernel_for(n);
+    cudaFuncAttributes fa;
+    if (cudaFuncGetAttributes(&fa, fn) != cudaSuccess || L.block > fa.maxThreadsPerBlock) {
+        cudaGetLastError();
+        return;
+    }
     if (L.smem > 48 * 1024 && cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, L.smem) != cudaSuccess) {
         cudaGetLastError();
         return;
@@ -438,6 +463,8 @@ static croft_status create_impl(croft_plan* out, int nx, int ny, int nz, croft_d
     p->d_status = NULL;
     p->conv_fused = false;
     p->conv_axis = -1;
+    const char* pdl_env = getenv("CROFT_PDL");  // 0: ordinary stream ordering between passes (for measurement)
+    p->pdl = !(pdl_env && pdl_env[0] == '0');
     const bool want_tc = dtype == CROFT_C2C_F32_TC_BF16X3;
     for (int axis = 0; axis < 3; ++axis) {
         const long long M = (axis == 2) ? 1 : (axis == 1 ? (long long)nz : (long long)ny * nz);
@@ -647,9 +674,13 @@ croft_status croft_plan_last_device_status(croft_plan plan) {
 
 // Launches passes [i0, i1) with the given sign.  A pass marked src_in reads `in`
 // unless force_out (every pass after the first logical one reads `out`).  With
-// evi, records the next timing event at the end of every logical pass.
+// evi, records the next timing event at the end of every logical pass.  Every
+// launch after the first of an exec (`started`) may use programmatic dependent
+// launch: it becomes resident while the previous pass drains and waits on the
+// device for that pass's results.  The first launch of an exec is ordered after
+// the caller's earlier work in the ordinary way.
 static croft_status run_passes(croft_plan plan, size_t i0, size_t i1, const void* in, void* out, cudaStream_t s,
-                               float isign, bool force_out, int* evi) {
+                               float isign, bool force_out, int* evi, bool& started) {
     for (size_t i = i0; i < i1; ++i) {
         PassLaunch L = plan->passes[i];
         L.args.isign = isign;
@@ -657,7 +688,9 @@ static croft_status run_passes(croft_plan plan, size_t i0, size_t i1, const void
         const size_t es = L.f64 ? sizeof(double2) : sizeof(float2);
         const char* src = ((L.src_in && !force_out) ? (const char*)in : (const char*)out) + (size_t)L.offset * es;
         char* dst = (char*)out + (size_t)L.offset * es;
-        if (launch_pass(L, src, dst, s) != cudaSuccess) { cudaGetLastError(); return CROFT_ERR_CUDA; }
+        const bool pdl = plan->pdl && started;
+        started = true;
+        if (launch_pass(L, src, dst, s, pdl) != cudaSuccess) { cudaGetLastError(); return CROFT_ERR_CUDA; }
         const bool group_end = (i + 1 == i1) || plan->passes[i + 1].group != L.group;
         if (evi && group_end && cudaEventRecord(plan->ev[(*evi)++], s) != cudaSuccess) {
             cudaGetLastError();
@@ -700,7 +733,8 @@ static croft_status exec_dir(croft_plan plan, const void* in, void* out, void* s
         if (cudaEventRecord(plan->ev[0], s) != cudaSuccess) { cudaGetLastError(); return CROFT_ERR_CUDA; }
         evi = 1;
     }
-    croft_status st = run_passes(plan, 0, plan->passes.size(), in, out, s, isign, false, tm ? &evi : nullptr);
+    bool started = false;
+    croft_status st = run_passes(plan, 0, plan->passes.size(), in, out, s, isign, false, tm ? &evi : nullptr, started);
     if (st != CROFT_OK) return st;
     plan->ev_count = tm ? evi : 0;
     plan->ran = true;
@@ -729,26 +763,34 @@ croft_status croft_exec_convolve(croft_plan plan, const void* in, void* out, con
         evi = 1;
     }
     croft_status st = CROFT_OK;
+    bool started = false;
     if (plan->conv_fused) {
         // forward passes but the last, the fused last-axis pass, backward passes of the other axes
         const size_t last = plan->passes.size() - 1;
-        st = run_passes(plan, 0, last, in, out, s, 1.0f, false, pe);
+        st = run_passes(plan, 0, last, in, out, s, 1.0f, false, pe, started);
         if (st != CROFT_OK) return st;
         const PassLaunch& L = plan->conv;
-        if (launch_conv(L, L.src_in ? in : out, out, g, s) != cudaSuccess) { cudaGetLastError(); return CROFT_ERR_CUDA; }
-        if (tm && cudaEventRecord(plan->ev[evi++], s) != cudaSuccess) { cudaGetLastError(); return CROFT_ERR_CUDA; }
-        st = run_passes(plan, 0, last, in, out, s, -1.0f, true, pe);
-        if (st != CROFT_OK) return st;
-    } else {
-        // F, multiply, B (a one-point grid has no passes: the multiply reads `in`)
-        st = run_passes(plan, 0, plan->passes.size(), in, out, s, 1.0f, false, pe);
-        if (st != CROFT_OK) return st;
-        if (launch_scale(plan->passes.empty() ? in : out, out, g, N, f64, s) != cudaSuccess) {
+        if (launch_conv(L, L.src_in ? in : out, out, g, s, plan->pdl && started) != cudaSuccess) {
             cudaGetLastError();
             return CROFT_ERR_CUDA;
         }
+        started = true;
         if (tm && cudaEventRecord(plan->ev[evi++], s) != cudaSuccess) { cudaGetLastError(); return CROFT_ERR_CUDA; }
-        st = run_passes(plan, 0, plan->passes.size(), in, out, s, -1.0f, true, pe);
+        st = run_passes(plan, 0, last, in, out, s, -1.0f, true, pe, started);
+        if (st != CROFT_OK) return st;
+    } else {
+        // F, multiply, B (a one-point grid has no passes: the multiply reads `in`)
+        st = run_passes(plan, 0, plan->passes.size(), in, out, s, 1.0f, false, pe, started);
+        if (st != CROFT_OK) return st;
+        // (after a tensor-core pass, which does not wait on the device, the multiply is ordered normally)
+        const bool pdl = plan->pdl && started && pass_supports_pdl(plan->passes.back());
+        if (launch_scale(plan->passes.empty() ? in : out, out, g, N, f64, s, pdl) != cudaSuccess) {
+            cudaGetLastError();
+            return CROFT_ERR_CUDA;
+        }
+        started = true;
+        if (tm && cudaEventRecord(plan->ev[evi++], s) != cudaSuccess) { cudaGetLastError(); return CROFT_ERR_CUDA; }
+        st = run_passes(plan, 0, plan->passes.size(), in, out, s, -1.0f, true, pe, started);
         if (st != CROFT_OK) return st;
     }
     plan->ev_count = tm ? evi : 0;

@@ -35,5 +35,6 @@ struct croft_plan_s {
     croft::PassLaunch conv;           // fused convolution pass (croft_conv_kernel.cuh), valid when conv_fused
     int conv_axis;                    // its axis (the plan's last pass)
     bool conv_fused;                  // false: croft_exec_convolve runs F, a multiply and B instead
+    bool pdl;                         // launches after the first of an exec use programmatic dependent launch
 };
 

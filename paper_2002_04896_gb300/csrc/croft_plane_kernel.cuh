@@ -107,6 +107,8 @@ __global__ void __launch_bounds__(PlaneShape<NY, NZ, C>::THREADS) croft_plane_ke
     }
     const long long plane = blockIdx.x / C;
     const long long off = plane * (long long)NY * NZ;
+    pdl_allow_dependents();
+    pdl_wait();
 
     // ---- z phase: rows rank*RY + r, one pencil per TZ threads --------------------
     {

@@ -93,3 +93,18 @@ CROFT_HD constexpr int croft_threads_per_pencil(int n) {
     while (p < t) p *= 2;
     return p;
 }
+
+// Column-tile width of the fused convolution pass (a compile-time constant of its
+// kernel) for length n and complex element size es bytes: 16 columns, widened
+// while the CTA stays within 256 threads; 8 for complex64 pencils of 32 threads
+// (four 256-thread CTAs per SM instead of two 512-thread ones); narrowed while
+// the CTA exceeds 512 threads or the data tile 100 KB.
+CROFT_HD constexpr int croft_conv_width(int n, int es) {
+    const int t = croft_threads_per_pencil(n);
+    int w = 16;
+    while (w * 2 * t <= 256) w *= 2;
+    if (es == 8 && t == 32) w = 8;
+    const long long tw_pad = ((n + 1) / 2) * 2;
+    while (w > 1 && (w * t > 512 || (tw_pad + (long long)n * w) * es > 100 * 1024)) w /= 2;
+    return w;
+}
