@@ -62,6 +62,8 @@ def kernel_source_sha() -> str:
     h = hashlib.sha256()
     csrc = os.path.join(ROOT, "paper_2002_04896_gb300", "csrc")
     for name in sorted(os.listdir(csrc)):
+        if not os.path.isfile(os.path.join(csrc, name)):
+            continue
         with open(os.path.join(csrc, name), "rb") as f:
             h.update(name.encode())
             h.update(f.read())
