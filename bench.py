@@ -256,7 +256,11 @@ def time_transform(croft, torch, stream, flush, plan, run_fwd, run_bwd, reps=5, 
     return statistics.median(fw), statistics.median(bw), pass_ms
 
 
-def measure_rows(croft, torch, dev, stream, flush, peak):
+ROW_NAMES = ("pme480_fp32", "pme384x360x320_fp32", "pme512_fp32", "pme512_tc_bf16x3", "pme256_convolve",
+             "f64_128", "f64_1024", "batch96")
+
+
+def measure_rows(croft, torch, dev, stream, flush, peak, only=None):  # noqa: PLR0915
     """The other hot-path rows, timed on device-generated data (timing does not depend on values):
     non-power-of-two meshes, FP32 vs tensor-core 512^3 (with the round-trip error of each),
     and the 96-grid batch (one persistent launch vs per-grid plans)."""
@@ -272,8 +276,13 @@ def measure_rows(croft, torch, dev, stream, flush, peak):
         return torch.complex(torch.rand(shape, device=dev, generator=gen) * 2 - 1,
                              torch.rand(shape, device=dev, generator=gen) * 2 - 1)
 
+    def want(name):
+        return only is None or name in only
+
     for name, shape, dtype in (("pme480_fp32", (480, 480, 480), 0), ("pme384x360x320_fp32", (384, 360, 320), 0),
                                ("pme512_fp32", (512, 512, 512), 0), ("pme512_tc_bf16x3", (512, 512, 512), 1)):
+        if not want(name):
+            continue
         x = grid(shape)
         y = torch.empty_like(x)
         z = torch.empty_like(x)
@@ -297,62 +306,65 @@ def measure_rows(croft, torch, dev, stream, flush, peak):
                       "dominant_pass_frac": (16.0 * n / (pass_ms[dom] * 1e-3) / 1e9) / peak,
                       "roundtrip_rel_l2": rt, "plan": desc}
         del x, y, z
-    # PME reciprocal-space convolution B(G * F(x)) on 256^3 with the smooth-PME influence function:
-    # croft_exec_convolve (last-axis forward * G * backward fused) vs forward, a torch multiply, backward
-    shape = (256, 256, 256)
-    n = math.prod(shape)
-    x = grid(shape)
-    y = torch.empty_like(x)
-    y2 = torch.empty_like(x)
-    g = torch.from_numpy(S.pme_influence(shape)).to(dev)
-    with croft.Plan(*shape) as p:
-        sh = stream.cuda_stream
-        t_conv, t_sep, pts = [], [], []
-        for i in range(2 + 5 + 5):
-            per_pass = i >= 7  # the last runs: per-pass events (kept out of the whole-pipeline times)
-            croft.croft_plan_set_timing(p.handle, per_pass)
-            for kind in ("conv", "sep"):
-                with torch.cuda.stream(stream):
-                    _flush(flush)
-                    a = torch.cuda.Event(enable_timing=True)
-                    b = torch.cuda.Event(enable_timing=True)
-                    a.record(stream)
-                    if kind == "conv":
-                        croft.croft_exec_convolve(p.handle, x, y, g, sh)
-                    else:
-                        croft.croft_exec_forward(p.handle, x, y2, sh)
-                        y2.mul_(g)
-                        croft.croft_exec_backward(p.handle, y2, y2, sh)
-                    b.record(stream)
-                pt = croft.croft_plan_pass_times(p.handle, 16) if (kind == "conv" and per_pass) else None
-                stream.synchronize()
-                if 2 <= i < 7:
-                    (t_conv if kind == "conv" else t_sep).append(a.elapsed_time(b))
-                if pt:
-                    pts.append(pt)
-        desc = p.describe()
-    stream.synchronize()
-    diff = float(torch.linalg.vector_norm((y - y2).flatten()) / torch.linalg.vector_norm(y2.flatten()))
-    tc_ms, ts_ms = statistics.median(t_conv), statistics.median(t_sep)
-    pass_ms = [statistics.mean(q[i] for q in pts) for i in range(len(pts[0]))] if pts else []
-    rows["pme256_convolve"] = {
-        "shape": list(shape), "ms": tc_ms, "gflops": 2 * nominal_flops(shape) / (tc_ms * 1e-3) / 1e9,
-        "pass_ms": pass_ms,
-        "fused_pass_ms": pass_ms[len(pass_ms) // 2] if pass_ms else None,
-        "fused_pass_frac": ((20.0 * n / (pass_ms[len(pass_ms) // 2] * 1e-3) / 1e9) / peak) if pass_ms else None,
-        "hbm_frac_compulsory": (20.0 * n / (tc_ms * 1e-3) / 1e9) / peak,
-        "hbm_frac_passes": (84.0 * n / (tc_ms * 1e-3) / 1e9) / peak,
-        "separate_ms": ts_ms, "speedup_vs_separate": ts_ms / tc_ms, "rel_diff_vs_separate": diff,
-        "plan": desc,
-        "notes": "fused: 4 plain passes (16N B each) + 1 fused pass (20N B: grid in/out + G); "
-                 "separate: 6 passes + torch's multiply (20N B)"}
-    del x, y, y2, g
+    if want("pme256_convolve"):
+        # PME reciprocal-space convolution B(G * F(x)) on 256^3 with the smooth-PME influence function:
+        # croft_exec_convolve (last-axis forward * G * backward fused) vs forward, a torch multiply, backward
+        shape = (256, 256, 256)
+        n = math.prod(shape)
+        x = grid(shape)
+        y = torch.empty_like(x)
+        y2 = torch.empty_like(x)
+        g = torch.from_numpy(S.pme_influence(shape)).to(dev)
+        with croft.Plan(*shape) as p:
+            sh = stream.cuda_stream
+            t_conv, t_sep, pts = [], [], []
+            for i in range(2 + 5 + 5):
+                per_pass = i >= 7  # the last runs: per-pass events (kept out of the whole-pipeline times)
+                croft.croft_plan_set_timing(p.handle, per_pass)
+                for kind in ("conv", "sep"):
+                    with torch.cuda.stream(stream):
+                        _flush(flush)
+                        a = torch.cuda.Event(enable_timing=True)
+                        b = torch.cuda.Event(enable_timing=True)
+                        a.record(stream)
+                        if kind == "conv":
+                            croft.croft_exec_convolve(p.handle, x, y, g, sh)
+                        else:
+                            croft.croft_exec_forward(p.handle, x, y2, sh)
+                            y2.mul_(g)
+                            croft.croft_exec_backward(p.handle, y2, y2, sh)
+                        b.record(stream)
+                    pt = croft.croft_plan_pass_times(p.handle, 16) if (kind == "conv" and per_pass) else None
+                    stream.synchronize()
+                    if 2 <= i < 7:
+                        (t_conv if kind == "conv" else t_sep).append(a.elapsed_time(b))
+                    if pt:
+                        pts.append(pt)
+            desc = p.describe()
+        stream.synchronize()
+        diff = float(torch.linalg.vector_norm((y - y2).flatten()) / torch.linalg.vector_norm(y2.flatten()))
+        tc_ms, ts_ms = statistics.median(t_conv), statistics.median(t_sep)
+        pass_ms = [statistics.mean(q[i] for q in pts) for i in range(len(pts[0]))] if pts else []
+        rows["pme256_convolve"] = {
+            "shape": list(shape), "ms": tc_ms, "gflops": 2 * nominal_flops(shape) / (tc_ms * 1e-3) / 1e9,
+            "pass_ms": pass_ms,
+            "fused_pass_ms": pass_ms[len(pass_ms) // 2] if pass_ms else None,
+            "fused_pass_frac": ((20.0 * n / (pass_ms[len(pass_ms) // 2] * 1e-3) / 1e9) / peak) if pass_ms else None,
+            "hbm_frac_compulsory": (20.0 * n / (tc_ms * 1e-3) / 1e9) / peak,
+            "hbm_frac_passes": (84.0 * n / (tc_ms * 1e-3) / 1e9) / peak,
+            "separate_ms": ts_ms, "speedup_vs_separate": ts_ms / tc_ms, "rel_diff_vs_separate": diff,
+            "plan": desc,
+            "notes": "fused: 4 plain passes (16N B each) + 1 fused pass (20N B: grid in/out + G); "
+                     "separate: 6 passes + torch's multiply (20N B)"}
+        del x, y, y2, g
     # complex128 at the paper's sizes (its Tables 1 and 3 time one double-complex forward transform)
     paper = {128: {"croft_best_s": 0.014, "croft_best_cores": 32, "fftw3_best_s": 0.019, "fftw3_best_cores": 32,
                    "source": "Table 1"},
              1024: {"croft_best_s": 1.2722, "croft_best_cores": 512, "fftw3_best_s": 4.7209, "fftw3_best_cores": 256,
                     "source": "Table 3"}}
     for n in (128, 1024):
+        if not want(f"f64_{n}"):
+            continue
         shape = (n, n, n)
         x = torch.complex(torch.rand(shape, device=dev, dtype=torch.float64, generator=gen) * 2 - 1,
                           torch.rand(shape, device=dev, dtype=torch.float64, generator=gen) * 2 - 1)
@@ -374,34 +386,35 @@ def measure_rows(croft, torch, dev, stream, flush, peak):
                             "paper_context": dict(paper[n], speedup_vs_croft_best=paper[n]["croft_best_s"] / (f_ms * 1e-3),
                                                   speedup_vs_fftw3_best=paper[n]["fftw3_best_s"] / (f_ms * 1e-3))}
         del x, y, z
-    # the batch of 96 uneven PME meshes (seed-3 sizes), one persistent launch vs per-grid plans
-    rng = np.random.default_rng(3)
-    dims = [tuple(int(v) for v in r) for r in rng.choice(np.asarray(S.BATCH_AXIS_CHOICES), size=(96, 3))]
-    xs = [grid(d) for d in dims]
-    ys = [torch.empty_like(x) for x in xs]
-    zs = [torch.empty_like(x) for x in xs]
-    total = sum(math.prod(d) for d in dims)
-    fl = sum(2 * nominal_flops(d) for d in dims)
-    brow = {"grids": 96, "points": total, "bytes_per_grid_set": 8 * total}
-    for mode, key in ((croft.CROFT_BATCH_ONE_LAUNCH, "one_launch"), (croft.CROFT_BATCH_PER_PASS, "per_pass"),
-                      (croft.CROFT_BATCH_PER_GRID, "per_grid")):
-        with croft.BatchPlan(dims, mode=mode) as bp:
-            croft.croft_plan_set_timing(bp.handle, True)
-            sh = stream.cuda_stream
-            f_ms, b_ms, _ = time_transform(
-                croft, torch, stream, flush, bp.handle,
-                lambda: croft.croft_exec_batched_forward(bp.handle, xs, ys, sh),
-                lambda: croft.croft_exec_batched_backward(bp.handle, ys, zs, sh))
-            launches = croft.croft_plan_num_launches(bp.handle)
-        t = f_ms + b_ms
-        brow[key] = {"ms_fwd": f_ms, "ms_bwd": b_ms, "gflops": fl / (t * 1e-3) / 1e9,
-                     "hbm_frac_whole_transform": (32.0 * total / (t * 1e-3) / 1e9) / peak,
-                     "launches_per_direction": launches}
-    stream.synchronize()
-    err = max(float(torch.linalg.vector_norm((z - math.prod(d) * x).flatten()) /
-                    torch.linalg.vector_norm((math.prod(d) * x).flatten())) for d, x, z in zip(dims, xs, zs))
-    brow["roundtrip_rel_l2_max"] = err
-    rows["batch96"] = brow
+    if want("batch96"):
+        # the batch of 96 uneven PME meshes (seed-3 sizes), one persistent launch vs per-grid plans
+        rng = np.random.default_rng(3)
+        dims = [tuple(int(v) for v in r) for r in rng.choice(np.asarray(S.BATCH_AXIS_CHOICES), size=(96, 3))]
+        xs = [grid(d) for d in dims]
+        ys = [torch.empty_like(x) for x in xs]
+        zs = [torch.empty_like(x) for x in xs]
+        total = sum(math.prod(d) for d in dims)
+        fl = sum(2 * nominal_flops(d) for d in dims)
+        brow = {"grids": 96, "points": total, "bytes_per_grid_set": 8 * total}
+        for mode, key in ((croft.CROFT_BATCH_ONE_LAUNCH, "one_launch"), (croft.CROFT_BATCH_PER_PASS, "per_pass"),
+                          (croft.CROFT_BATCH_PER_GRID, "per_grid")):
+            with croft.BatchPlan(dims, mode=mode) as bp:
+                croft.croft_plan_set_timing(bp.handle, True)
+                sh = stream.cuda_stream
+                f_ms, b_ms, _ = time_transform(
+                    croft, torch, stream, flush, bp.handle,
+                    lambda: croft.croft_exec_batched_forward(bp.handle, xs, ys, sh),
+                    lambda: croft.croft_exec_batched_backward(bp.handle, ys, zs, sh))
+                launches = croft.croft_plan_num_launches(bp.handle)
+            t = f_ms + b_ms
+            brow[key] = {"ms_fwd": f_ms, "ms_bwd": b_ms, "gflops": fl / (t * 1e-3) / 1e9,
+                         "hbm_frac_whole_transform": (32.0 * total / (t * 1e-3) / 1e9) / peak,
+                         "launches_per_direction": launches}
+        stream.synchronize()
+        err = max(float(torch.linalg.vector_norm((z - math.prod(d) * x).flatten()) /
+                        torch.linalg.vector_norm((math.prod(d) * x).flatten())) for d, x, z in zip(dims, xs, zs))
+        brow["roundtrip_rel_l2_max"] = err
+        rows["batch96"] = brow
     return rows
 
 
@@ -566,7 +579,8 @@ def run_croft(args):
 
     rows = None
     if rank == 0 and not args.no_rows:
-        rows = measure_rows(croft, torch, dev, stream, flush, peak)
+        only = None if args.rows == "all" else set(args.rows.split(","))
+        rows = measure_rows(croft, torch, dev, stream, flush, peak, only)
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
@@ -632,6 +646,8 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--schedule", default="auto", choices=["auto", "three_pass", "plane_fused", "slab_l2"])
     ap.add_argument("--no-rows", action="store_true", help="skip the extra per-row measurements")
+    ap.add_argument("--rows", default="all",
+                    help="comma-separated subset of the extra rows (" + ", ".join(ROW_NAMES) + ") or 'all'")
     ap.add_argument("--clock-window-s", type=float, default=2.0,
                     help="minimum wall time of the timed region, padded with untimed L2-flush writes "
                          "between steps (0 under a profiler)")

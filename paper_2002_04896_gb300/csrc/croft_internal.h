@@ -94,11 +94,11 @@ const PlaneKernel* find_plane_kernel(int ny, int nz, int cluster);
 pipe_fn lookup_pipe_kernel_group_0(int layout, int n);
 pipe_fn lookup_pipe_kernel_group_1(int layout, int n);
 
-// croft_kernels.cu, one per size group
-pass_fn lookup_pass_kernel_group_0(int layout, int n);
-pass_fn lookup_pass_kernel_group_1(int layout, int n);
-pass_fn lookup_pass_kernel_group_2(int layout, int n);
-pass_fn lookup_pass_kernel_group_3(int layout, int n);
+// croft_kernels.cu, one per size group (w: the COL tile width; ignored for ROW)
+pass_fn lookup_pass_kernel_group_0(int layout, int n, int w);
+pass_fn lookup_pass_kernel_group_1(int layout, int n, int w);
+pass_fn lookup_pass_kernel_group_2(int layout, int n, int w);
+pass_fn lookup_pass_kernel_group_3(int layout, int n, int w);
 
 // croft_tc.cu: tensor-core pass kernels (NULL when n has no instantiation)
 pass_fn tc_pass_kernel_for(int layout, int n);
@@ -110,8 +110,9 @@ void dev_free(void* p);
 cudaError_t host_alloc(void** p, size_t bytes);
 void host_free(void* p);
 
-// croft_kernels64.cu: complex128 pass kernels (NULL when n has no instantiation)
-pass64_fn pass64_kernel_for(int layout, int n);
+// croft_kernels64.cu: complex128 pass kernels (NULL when n has no instantiation; w: COL tile
+// width, 0 = the default one)
+pass64_fn pass64_kernel_for(int layout, int n, int w = 0);
 
 // croft_conv.cu: fused convolution pass kernels (NULL when n has no instantiation)
 conv_fn lookup_conv_kernel_group_0(int n);
@@ -124,7 +125,7 @@ cudaError_t launch_scale(const void* in, void* out, const void* g, long long n, 
                          bool pdl = false);
 
 // croft_passes.cu
-pass_fn pass_kernel_for(int layout, int n);
+pass_fn pass_kernel_for(int layout, int n, int w);
 conv_fn conv_kernel_for(int n);
 pipe_fn pipe_kernel_for(int layout, int n);
 int pipe_blocks_per_sm(const PassLaunch& L);

@@ -11,11 +11,17 @@
 
 namespace croft {
 
-pass64_fn pass64_kernel_for(int layout, int n) {
+// (complex128 COL tiles take one width whatever the stride: croft_col_width(N, 16, *))
+template <int N>
+static pass64_fn col64_kernel(int w) {
+    constexpr int W = croft_col_width(N, 16, false);
+    return (w == W || w == 0) ? croft_pass_kernel<LAYOUT_COL, N, double2, W> : nullptr;
+}
+
+pass64_fn pass64_kernel_for(int layout, int n, int w) {
 #define CROFT_CASE64(N)                                                                 \
     case N:                                                                             \
-        return layout == LAYOUT_ROW ? croft_pass_kernel<LAYOUT_ROW, N, double2>         \
-                                    : croft_pass_kernel<LAYOUT_COL, N, double2>;
+        return layout == LAYOUT_ROW ? croft_pass_kernel<LAYOUT_ROW, N, double2> : col64_kernel<N>(w);
     switch (n) {
         CROFT_SIZES64(CROFT_CASE64)
         default: return nullptr;

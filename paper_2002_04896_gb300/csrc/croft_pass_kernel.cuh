@@ -27,7 +27,9 @@ namespace croft {
 
 // Shared memory: [twiddles: tw_pad elements][tile: W pencils].  C = float2
 // (complex64, the default) or double2 (complex128, twiddles from A.tw64).
-template <int LAYOUT, int N, class C = float2>
+// COL kernels are specialised on the column-tile width WC as well (so the
+// shared-memory indices fold into constants); ROW kernels take W from A.W.
+template <int LAYOUT, int N, class C = float2, int WC = 0>
 __global__ void __launch_bounds__(512) croft_pass_kernel(const C* in, C* out, const __grid_constant__ PassArgs A) {
     constexpr int T = croft_threads_per_pencil(N);
     extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -51,14 +53,15 @@ __global__ void __launch_bounds__(512) croft_pass_kernel(const C* in, C* out, co
         fft_pencil_row<N, T>(GlobalInUnitT<C>{in + base, A.isign}, sbuf + c * croft_row_ld_staged(N),
                              GlobalOutUnitT<C>{out + base, A.isign}, stw, lane, ok);
     } else {
-        const int c = threadIdx.x % A.W;
-        const int lane = threadIdx.x / A.W;
-        const long long col = (long long)blockIdx.x * A.W + c;
+        static_assert(LAYOUT == LAYOUT_ROW || WC > 0, "COL kernels need a compile-time tile width");
+        const int c = threadIdx.x % WC;
+        const int lane = threadIdx.x / WC;
+        const long long col = (long long)blockIdx.x * WC + c;
         const bool ok = col < A.ncols;
         const long long b = col / A.M;
         const long long m = col - b * A.M;
         const long long base = b * (long long)N * A.M + m;
-        fft_pencil<N, T>(GlobalInT<C>{in + base, A.M, A.isign}, SmemColT<C>{sbuf + c, A.W},
+        fft_pencil<N, T>(GlobalInT<C>{in + base, A.M, A.isign}, SmemColFixed<C, (WC > 0 ? WC : 1)>{sbuf + c},
                          GlobalOutT<C>{out + base, A.M, A.isign}, stw, lane, ok);
     }
 }

@@ -58,11 +58,11 @@ int pipe_blocks_per_sm(const PassLaunch& L) {
     return n;
 }
 
-pass_fn pass_kernel_for(int layout, int n) {
-    pass_fn f = lookup_pass_kernel_group_0(layout, n);
-    if (!f) f = lookup_pass_kernel_group_1(layout, n);
-    if (!f) f = lookup_pass_kernel_group_2(layout, n);
-    if (!f) f = lookup_pass_kernel_group_3(layout, n);
+pass_fn pass_kernel_for(int layout, int n, int w) {
+    pass_fn f = lookup_pass_kernel_group_0(layout, n, w);
+    if (!f) f = lookup_pass_kernel_group_1(layout, n, w);
+    if (!f) f = lookup_pass_kernel_group_2(layout, n, w);
+    if (!f) f = lookup_pass_kernel_group_3(layout, n, w);
     return f;
 }
 
@@ -139,12 +139,12 @@ cudaError_t prepare_pass(const PassLaunch& L) {
         return cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, L.smem);
     }
     if (L.f64) {
-        pass64_fn f = pass64_kernel_for(L.layout, L.args.n);
+        pass64_fn f = pass64_kernel_for(L.layout, L.args.n, L.args.W);
         if (!f) return cudaErrorInvalidValue;
         if (L.smem <= 48 * 1024) return cudaSuccess;
         return cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, L.smem);
     }
-    pass_fn f = L.tc ? tc_pass_kernel_for(L.layout, L.args.n) : pass_kernel_for(L.layout, L.args.n);
+    pass_fn f = L.tc ? tc_pass_kernel_for(L.layout, L.args.n) : pass_kernel_for(L.layout, L.args.n, L.args.W);
     if (!f) return cudaErrorInvalidValue;
     if (L.smem <= 48 * 1024) return cudaSuccess;
     return cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, L.smem);
@@ -153,7 +153,7 @@ cudaError_t prepare_pass(const PassLaunch& L) {
 cudaError_t launch_pass(const PassLaunch& L, const void* vin, void* vout, cudaStream_t s, bool pdl) {
     pdl = pdl && pass_supports_pdl(L);
     if (L.f64) {
-        pass64_fn f = pass64_kernel_for(L.layout, L.args.n);
+        pass64_fn f = pass64_kernel_for(L.layout, L.args.n, L.args.W);
         if (!f) return cudaErrorInvalidValue;
         return launch_ex(f, L, s, pdl, (const double2*)vin, (double2*)vout, L.args);
     }
@@ -181,7 +181,7 @@ cudaError_t launch_pass(const PassLaunch& L, const void* vin, void* vout, cudaSt
         f<<<L.grid, L.block, L.smem, s>>>(in, out, L.args);
         return cudaGetLastError();
     }
-    pass_fn f = pass_kernel_for(L.layout, L.args.n);
+    pass_fn f = pass_kernel_for(L.layout, L.args.n, L.args.W);
     if (!f) return cudaErrorInvalidValue;
     return launch_ex(f, L, s, pdl, in, out, L.args);
 }

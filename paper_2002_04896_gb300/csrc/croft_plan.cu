@@ -156,13 +156,11 @@ static bool shape_pass(PassLaunch& L, int layout, int n, long long M, long long 
         L.smem = (int)((A.tw_pad + (long long)W * ld) * es);
     } else {
         int W = 16;
-        while (W * 2 * T <= 256) W *= 2;
-        // Pencils of 32 threads (lengths of a few hundred): 16 columns make 512-thread CTAs,
-        // two per SM (registers).  Where the rows of a pencil are close (axis stride up to
-        // 64 KB) 8 columns - 256-thread CTAs, four per SM - measured faster (y pass of 480^3:
-        // 457 -> 409 us); across long strides (the x pass) the 64-byte row segments cost more
-        // than the occupancy gains (480^3: 463 -> 514 us), so 16 stays.
-        if (!tc && !f64 && T == 32 && M * es <= 64 * 1024) W = 8;
+        if (tc) {
+            while (W * 2 * T <= 256) W *= 2;
+        } else {
+            W = croft_col_width(n, (int)es, M * es <= 64 * 1024);  // the width the kernels are built for
+        }
         if (want_w >= 1 && !tc) W = want_w;
         while (W > 1 && (W * T > max_threads || (A.tw_pad + (long long)n * W) * es > smem_cap)) W /= 2;
         A.W = W;
@@ -314,7 +312,9 @@ static croft_status add_axis_pass(croft_plan p, int axis, int x0 = 0, int nxs = 
         }
     }
     PassLaunch L;
-    const int want_w = layout == LAYOUT_COL ? env_width(axis == 1 ? "CROFT_COL_W_Y" : "CROFT_COL_W_X", "CROFT_COL_W") : 0;
+    // (tuning override of the COL tile width; honoured only for a width a kernel is built for)
+    int want_w = layout == LAYOUT_COL ? env_width(axis == 1 ? "CROFT_COL_W_Y" : "CROFT_COL_W_X", "CROFT_COL_W") : 0;
+    if (want_w && (f64 ? !pass64_kernel_for(layout, n, want_w) : !pass_kernel_for(layout, n, want_w))) want_w = 0;
     if (!shape_pass(L, layout, n, M, N / n, p->axis_tc[axis], f64, want_w)) return CROFT_ERR_UNSUPPORTED_SIZE;
     L.kind = PASS_AXIS;
     L.args.tw = p->tw_dev[axis];

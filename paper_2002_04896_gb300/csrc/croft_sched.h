@@ -94,17 +94,27 @@ CROFT_HD constexpr int croft_threads_per_pencil(int n) {
     return p;
 }
 
-// Column-tile width of the fused convolution pass (a compile-time constant of its
-// kernel) for length n and complex element size es bytes: 16 columns, widened
-// while the CTA stays within 256 threads; 8 for complex64 pencils of 32 threads
-// (four 256-thread CTAs per SM instead of two 512-thread ones); narrowed while
-// the CTA exceeds 512 threads or the data tile 100 KB.
-CROFT_HD constexpr int croft_conv_width(int n, int es) {
+// Column-tile width (columns per CTA) of a COL pass - a compile-time constant of
+// its kernel - for length n, complex element size es bytes, and whether the rows
+// of a pencil are close in memory (axis stride of at most 64 KB).  16 columns
+// (128-byte rows), widened while the CTA stays within 256 threads.  Complex64
+// pencils of 32 threads (lengths of a few hundred) take 8 columns when the rows
+// are close: 256-thread CTAs, four per SM instead of two 512-thread ones by
+// registers (y pass of 480^3: 457 -> 409 us); across long strides the 64-byte
+// row segments cost more than the occupancy gains (x pass of 480^3: 463 -> 514
+// us), so 16 stays.  Narrowed while the CTA exceeds 512 threads or the data tile
+// 100 KB.
+CROFT_HD constexpr int croft_col_width(int n, int es, bool near_rows) {
     const int t = croft_threads_per_pencil(n);
     int w = 16;
     while (w * 2 * t <= 256) w *= 2;
-    if (es == 8 && t == 32) w = 8;
+    if (es == 8 && t == 32 && near_rows) w = 8;
     const long long tw_pad = ((n + 1) / 2) * 2;
     while (w > 1 && (w * t > 512 || (tw_pad + (long long)n * w) * es > 100 * 1024)) w /= 2;
     return w;
 }
+
+// Column-tile width of the fused convolution pass: the near-rows width whatever the
+// stride - that pass does twice the arithmetic per byte, so occupancy matters more
+// (480^3: 927 -> 801 us with 8 columns).
+CROFT_HD constexpr int croft_conv_width(int n, int es) { return croft_col_width(n, es, true); }
