@@ -397,7 +397,7 @@ def measure_rows(croft, torch, dev, stream, flush, peak, only=None):  # noqa: PL
         fl = sum(2 * nominal_flops(d) for d in dims)
         brow = {"grids": 96, "points": total, "bytes_per_grid_set": 8 * total}
         for mode, key in ((croft.CROFT_BATCH_ONE_LAUNCH, "one_launch"), (croft.CROFT_BATCH_PER_PASS, "per_pass"),
-                          (croft.CROFT_BATCH_PER_GRID, "per_grid")):
+                          (croft.CROFT_BATCH_PER_GRID, "per_grid"), (croft.CROFT_BATCH_GROUPED, "grouped")):
             with croft.BatchPlan(dims, mode=mode) as bp:
                 croft.croft_plan_set_timing(bp.handle, True)
                 sh = stream.cuda_stream

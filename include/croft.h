@@ -129,7 +129,13 @@ croft_status croft_plan_create_schedule(croft_plan* out, int nx, int ny, int nz,
  *               one CTA per tile, ordered by kernel boundaries; CUDA graph per
  *               direction.
  *           CROFT_BATCH_PER_GRID  - one single-grid plan per grid, launched in turn.
- *           CROFT_BATCH_AUTO      - time the three on scratch buffers at creation
+ *           CROFT_BATCH_GROUPED   - per pass, one launch per distinct axis length,
+ *               covering the tiles of every grid with that length (the
+ *               single-grid pass kernel specialised on the length, with a
+ *               per-CTA grid lookup); the launches of one pass run concurrently
+ *               and the passes are ordered by the edges of a CUDA graph per
+ *               direction.
+ *           CROFT_BATCH_AUTO      - time the four on scratch buffers at creation
  *               and keep the fastest; the choice is cached in the text file named
  *               by $CROFT_TUNE_CACHE (default $HOME/.croft_tune_cache.txt), keyed by
  *               the sizes, GPU name and CUDA runtime version.  CROFT_TUNE=off skips
@@ -148,7 +154,8 @@ typedef enum {
     CROFT_BATCH_AUTO = 0,
     CROFT_BATCH_ONE_LAUNCH = 1,
     CROFT_BATCH_PER_PASS = 2,
-    CROFT_BATCH_PER_GRID = 3
+    CROFT_BATCH_PER_GRID = 3,
+    CROFT_BATCH_GROUPED = 4
 } croft_batch_mode;
 
 croft_status croft_plan_create_batched(croft_plan* out, int count, const int* dims, croft_dtype dtype);

@@ -36,6 +36,7 @@ CROFT_BATCH_AUTO = 0
 CROFT_BATCH_ONE_LAUNCH = 1
 CROFT_BATCH_PER_PASS = 2
 CROFT_BATCH_PER_GRID = 3
+CROFT_BATCH_GROUPED = 4
 
 CROFT_OK = 0
 CROFT_ERR_INVALID_ARG = 1

@@ -6,8 +6,11 @@
 //   PER_PASS   : the same work list in three launches (z, y, x) of one CTA per
 //                tile; kernel boundaries order the passes, no counters, no waits;
 //   PER_GRID   : one ordinary single-grid plan per grid, launched one after
-//                the other (the plain baseline).
-// ONE_LAUNCH and PER_PASS are recorded once into a CUDA graph per direction
+//                the other (the plain baseline);
+//   GROUPED    : per pass, one launch per distinct axis length over every grid
+//                that has it (croft_batch_group.cu), the launches of a pass
+//                concurrent.
+// ONE_LAUNCH, PER_PASS and GROUPED are recorded once into a CUDA graph per direction
 // (descriptor upload from pinned memory, counter reset, kernel launch(es));
 // an exec fills in the grids' pointers and launches the graph.  AUTO times the
 // three schedules on scratch buffers at plan creation and keeps the fastest,
@@ -42,6 +45,13 @@ int batched_blocks_per_sm(int smem);
 void* batched_kernel_ptr();
 int host_build_twiddles(int n, float* out);  // croft_plan.cu
 
+struct GroupState;  // croft_batch_group.cu
+croft_status group_state_build(const std::vector<int>& dims, const std::vector<int>& pgrid, GroupState** out);
+void group_state_destroy(GroupState* s);
+void group_state_fill(GroupState* s, void* const* in, void* const* out);
+croft_status group_graph_add(GroupState* s, cudaGraph_t g, float isign);
+int group_state_launches(const GroupState* s);
+
 struct BatchState {
     int count = 0;
     std::vector<int> dims;
@@ -68,7 +78,8 @@ struct BatchState {
     // grids on single-grid plans (axes > 128, or PER_GRID mode)
     std::vector<int> sgrid;
     std::vector<croft_plan> subplans;
-    double tuned_us[4] = {0, 0, 0, 0};
+    GroupState* group = nullptr;      // GROUPED schedule
+    double tuned_us[5] = {0, 0, 0, 0, 0};
 };
 
 void batch_state_destroy(BatchState* b) {
@@ -84,6 +95,7 @@ void batch_state_destroy(BatchState* b) {
     dev_free(b->d_tw);
     dev_free(b->d_scratch);
     for (croft_plan p : b->subplans) croft_plan_destroy(p);
+    group_state_destroy(b->group);
     delete b;
 }
 
@@ -223,6 +235,12 @@ static croft_status build_graphs(BatchState* b) {
         cudaGraph_t g;
         if (cudaGraphCreate(&g, 0) != cudaSuccess) return CROFT_ERR_CUDA;
         b->graph[d] = g;
+        if (b->mode == CROFT_BATCH_GROUPED) {
+            croft_status st = group_graph_add(b->group, g, isign);
+            if (st != CROFT_OK) return st;
+            if (cudaGraphInstantiate(&b->gexec[d], g, 0) != cudaSuccess) return CROFT_ERR_CUDA;
+            continue;
+        }
         cudaGraphNode_t up, rs;
         if (cudaGraphAddMemcpyNode1D(&up, g, nullptr, 0, b->d_grids, b->staging, sizeof(BatchGrid) * G,
                                      cudaMemcpyHostToDevice) != cudaSuccess)
@@ -286,9 +304,13 @@ static croft_status exec_batch(croft_plan plan, void* const* in, void* const* ou
             cudaGetLastError();
             return CROFT_ERR_CUDA;
         }
-        for (size_t i = 0; i < b->pgrid.size(); ++i) {
-            b->staging[i].in = (const float2*)in[b->pgrid[i]];
-            b->staging[i].out = (float2*)out[b->pgrid[i]];
+        if (b->mode == CROFT_BATCH_GROUPED) {
+            group_state_fill(b->group, in, out);
+        } else {
+            for (size_t i = 0; i < b->pgrid.size(); ++i) {
+                b->staging[i].in = (const float2*)in[b->pgrid[i]];
+                b->staging[i].out = (float2*)out[b->pgrid[i]];
+            }
         }
         if (cudaGraphLaunch(b->gexec[dir], s) != cudaSuccess) { cudaGetLastError(); return CROFT_ERR_CUDA; }
         if (cudaEventRecord(b->staging_free, s) != cudaSuccess) { cudaGetLastError(); return CROFT_ERR_CUDA; }
@@ -324,7 +346,7 @@ static std::string tune_key(const BatchState* b) {
     cudaDeviceProp prop;
     cudaGetDeviceProperties(&prop, dev);
     char buf[512];
-    snprintf(buf, sizeof(buf), "batch-v1:%d:%016llx:%s:%d", b->count, h, prop.name, rt);
+    snprintf(buf, sizeof(buf), "batch-v2:%d:%016llx:%s:%d", b->count, h, prop.name, rt);
     for (char* c = buf; *c; ++c)
         if (*c == ' ' || *c == '"') *c = '_';
     return buf;
@@ -354,7 +376,8 @@ static int tune_lookup(const std::string& key) {
 static void tune_store(const std::string& key, int mode, const double* us) {
     FILE* f = fopen(tune_cache_path().c_str(), "a");
     if (!f) return;
-    fprintf(f, "%s %d one_launch_us=%.1f per_pass_us=%.1f per_grid_us=%.1f\n", key.c_str(), mode, us[1], us[2], us[3]);
+    fprintf(f, "%s %d one_launch_us=%.1f per_pass_us=%.1f per_grid_us=%.1f grouped_us=%.1f\n", key.c_str(), mode, us[1],
+            us[2], us[3], us[4]);
     fclose(f);
 }
 
@@ -378,7 +401,14 @@ static croft_status configure(BatchState* b, int mode) {
         if (st != CROFT_OK) return st;
         b->subplans.push_back(sp);
     }
-    if (!b->d_items && !b->pgrid.empty()) {
+    if (mode == CROFT_BATCH_GROUPED) {
+        if (!b->group && !b->pgrid.empty()) {
+            croft_status st = group_state_build(b->dims, b->pgrid, &b->group);
+            if (st != CROFT_OK) return st;
+        }
+        if (!b->staging_free && cudaEventCreateWithFlags(&b->staging_free, cudaEventDisableTiming) != cudaSuccess)
+            return CROFT_ERR_CUDA;
+    } else if (!b->d_items && !b->pgrid.empty()) {
         croft_status st = build_persistent(b);
         if (st != CROFT_OK) return st;
     }
@@ -390,7 +420,7 @@ static croft_status autotune(croft_plan plan) {
     BatchState* b = plan->batch;
     const std::string key = tune_key(b);
     int cached = tune_lookup(key);
-    if (cached >= CROFT_BATCH_ONE_LAUNCH && cached <= CROFT_BATCH_PER_GRID) return configure(b, cached);
+    if (cached >= CROFT_BATCH_ONE_LAUNCH && cached <= CROFT_BATCH_GROUPED) return configure(b, cached);
     size_t total = 0;
     std::vector<size_t> offs;
     for (int g = 0; g < b->count; ++g) {
@@ -410,7 +440,7 @@ static croft_status autotune(croft_plan plan) {
     cudaEvent_t e0, e1;
     cudaEventCreate(&e0);
     cudaEventCreate(&e1);
-    const int modes[3] = {CROFT_BATCH_ONE_LAUNCH, CROFT_BATCH_PER_PASS, CROFT_BATCH_PER_GRID};
+    const int modes[4] = {CROFT_BATCH_ONE_LAUNCH, CROFT_BATCH_PER_PASS, CROFT_BATCH_PER_GRID, CROFT_BATCH_GROUPED};
     double best = 1e30;
     int best_mode = CROFT_BATCH_ONE_LAUNCH;
     croft_status st = CROFT_OK;
@@ -461,7 +491,7 @@ croft_status croft_plan_create_batched_mode(croft_plan* out, int count, const in
     *out = NULL;
     if (count < 1 || !dims) return CROFT_ERR_INVALID_ARG;
     if (dtype != CROFT_C2C_F32) return dtype == CROFT_C2C_F32_TC_BF16X3 ? CROFT_ERR_UNSUPPORTED_SIZE : CROFT_ERR_INVALID_ARG;
-    if (mode < CROFT_BATCH_AUTO || mode > CROFT_BATCH_PER_GRID) return CROFT_ERR_INVALID_ARG;
+    if (mode < CROFT_BATCH_AUTO || mode > CROFT_BATCH_GROUPED) return CROFT_ERR_INVALID_ARG;
     for (int i = 0; i < 3 * count; ++i)
         if (croft_make_sched(dims[i]).count < 0) return CROFT_ERR_UNSUPPORTED_SIZE;
     int dev = 0;
@@ -560,20 +590,22 @@ size_t batch_workspace_bytes(const croft_plan_s* p) {
 int batch_num_launches(const croft_plan_s* p) {
     const BatchState* b = p->batch;
     int n = 0;
-    if (!b->pgrid.empty()) n += (b->mode == CROFT_BATCH_PER_PASS) ? 3 : 1;
+    if (!b->pgrid.empty())
+        n += b->mode == CROFT_BATCH_PER_PASS ? 3 : (b->mode == CROFT_BATCH_GROUPED ? group_state_launches(b->group) : 1);
     for (croft_plan sp : b->subplans) n += croft_plan_num_launches(sp);
     return n;
 }
 
 std::string batch_describe(const croft_plan_s* p) {
     const BatchState* b = p->batch;
-    static const char* names[4] = {"auto", "one_launch", "per_pass", "per_grid"};
+    static const char* names[5] = {"auto", "one_launch", "per_pass", "per_grid", "grouped"};
     char tmp[512];
     snprintf(tmp, sizeof(tmp),
-             "batch of %d grids, schedule %s (persistent grids %d, items %d, blocks %d, smem %d; single-grid plans %d)"
-             " tuned_us one_launch=%.1f per_pass=%.1f per_grid=%.1f",
-             b->count, names[b->mode], (int)b->pgrid.size(), b->nitems, b->blocks, b->smem, (int)b->subplans.size(),
-             b->tuned_us[1], b->tuned_us[2], b->tuned_us[3]);
+             "batch of %d grids, schedule %s (persistent grids %d, items %d, blocks %d, smem %d; grouped launches %d;"
+             " single-grid plans %d) tuned_us one_launch=%.1f per_pass=%.1f per_grid=%.1f grouped=%.1f",
+             b->count, names[b->mode], (int)b->pgrid.size(), b->nitems, b->blocks, b->smem,
+             group_state_launches(b->group), (int)b->subplans.size(), b->tuned_us[1], b->tuned_us[2], b->tuned_us[3],
+             b->tuned_us[4]);
     return tmp;
 }
 

@@ -22,3 +22,10 @@
 // 1024 and a few mixed-radix ones.
 #define CROFT_SIZES64(X) \
     X(2) X(3) X(4) X(5) X(6) X(8) X(10) X(12) X(15) X(16) X(32) X(48) X(60) X(64) X(96) X(120) X(128) X(256) X(512) X(1024)
+
+// Batched plans: every axis length <= 128 of the form 2^a 3^b 5^c (the per-system PME
+// mesh range; croft_batched.cu, croft_batch_group.cu).
+#define CROFT_BATCH_SIZES(X)                                                                                \
+    X(2) X(3) X(4) X(5) X(6) X(8) X(9) X(10) X(12) X(15) X(16) X(18) X(20) X(24) X(25) X(27) X(30) X(32)     \
+    X(36) X(40) X(45) X(48) X(50) X(54) X(60) X(64) X(72) X(75) X(80) X(81) X(90) X(96) X(100) X(108)       \
+    X(120) X(125) X(128)

@@ -26,7 +26,7 @@ def mixed_inputs():
     return [(rng.uniform(-1, 1, d) + 1j * rng.uniform(-1, 1, d)).astype(np.complex64) for d in MIXED]
 
 
-@pytest.mark.parametrize("mode", [1, 2, 3])
+@pytest.mark.parametrize("mode", [1, 2, 3, 4])
 def test_mixed_batch_every_mode_matches_oracle(croft_lib, mixed_inputs, mode):
     ins = [torch.from_numpy(x).cuda() for x in mixed_inputs]
     with croft_lib.BatchPlan(MIXED, mode=mode) as bp:
@@ -83,6 +83,32 @@ def test_pme_batch_96_one_launch_vs_oracle_and_per_grid(croft_lib, pme_batch):
     print(f"pme batch of 96: worst error / tolerance = {worst:.3e}")
 
 
+def test_pme_batch_96_grouped_matches_single_grid_plans_bitwise(croft_lib, pme_batch):
+    """The grouped schedule runs the single-grid pass kernels' arithmetic: the same bits as per-grid plans."""
+    dims, grids = pme_batch
+    ins = [torch.from_numpy(g).cuda() for g in grids]
+    with croft_lib.BatchPlan(dims, mode=croft_lib.CROFT_BATCH_GROUPED) as gp, \
+            croft_lib.BatchPlan(dims, mode=croft_lib.CROFT_BATCH_PER_GRID) as pg:
+        a = gp.forward(ins)
+        b = pg.forward(ins)
+        ra = gp.backward(a)
+        rb = pg.backward(b)
+        c = [t.clone() for t in ins]
+        gp.forward(c, c)  # in place
+        torch.cuda.synchronize()
+        n_len = len({d[a] for d in dims for a in range(3)})
+        assert 3 <= croft_lib.croft_plan_num_launches(gp.handle) <= 3 * n_len
+        assert "grouped" in gp.describe()
+    for g in range(len(grids)):
+        assert torch.equal(a[g].view(torch.int32), b[g].view(torch.int32)), (g, dims[g])
+        assert torch.equal(ra[g].view(torch.int32), rb[g].view(torch.int32)), (g, dims[g])
+        assert torch.equal(a[g].view(torch.int32), c[g].view(torch.int32)), (g, dims[g])
+    # and against the oracle on a sample of the grids
+    for g in range(0, len(grids), 12):
+        x = grids[g]
+        assert oracle.rel_l2(a[g].cpu().numpy(), oracle.forward(x)) <= tol(x.shape)
+
+
 def test_autotune_chooses_and_caches(croft_lib, pme_batch, tmp_path, monkeypatch):
     dims, _ = pme_batch
     cache = tmp_path / "tune.txt"
@@ -93,10 +119,10 @@ def test_autotune_chooses_and_caches(croft_lib, pme_batch, tmp_path, monkeypatch
         desc = bp.describe()
     assert cache.exists()
     line = cache.read_text().strip().splitlines()[-1]
-    assert line.startswith("batch-v1:24:") and "one_launch_us=" in line
+    assert line.startswith("batch-v2:24:") and "one_launch_us=" in line and "grouped_us=" in line
     mode = int(line.split()[1])
-    assert mode in (1, 2, 3)
-    assert ["one_launch", "per_pass", "per_grid"][mode - 1] in desc
+    assert mode in (1, 2, 3, 4)
+    assert ["one_launch", "per_pass", "per_grid", "grouped"][mode - 1] in desc
     print(desc)
     # a second plan reads the cache (no new line appended)
     with croft_lib.BatchPlan(sub):
