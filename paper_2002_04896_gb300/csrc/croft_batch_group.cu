@@ -109,7 +109,7 @@ croft_status group_state_build(const std::vector<int>& dims, const std::vector<i
             L.pass = p;
             L.layout = layout;
             L.n = n;
-            L.W = layout == LAYOUT_ROW ? 256 / T : croft_col_width(n, 8, true);
+            L.W = layout == LAYOUT_ROW ? 256 / T : croft_col_width(n, 8);
             L.block = L.W * T;
             const long long tile_elems = layout == LAYOUT_ROW ? (long long)L.W * croft_row_ld_staged(n) : (long long)n * L.W;
             L.smem = (int)((tw_pad + tile_elems) * sizeof(float2));

@@ -32,7 +32,7 @@ struct GroupArgs {
 };
 
 // ROW launches: W = 256 / T pencils per CTA; COL launches: the compile-time width
-// croft_col_width(N) (rows are never far apart in a mesh of axes <= 128 x 128).
+// croft_col_width(N).
 template <int LAYOUT, int N>
 __global__ void __launch_bounds__(256) croft_group_kernel(const __grid_constant__ GroupArgs A) {
     constexpr int T = croft_threads_per_pencil(N);
@@ -53,7 +53,7 @@ __global__ void __launch_bounds__(256) croft_group_kernel(const __grid_constant_
         fft_pencil_row<N, T>(GlobalInUnit{S.in + base, A.isign}, sbuf + c * croft_row_ld_staged(N),
                              GlobalOutUnit{S.out + base, A.isign}, stw, lane, ok);
     } else {
-        constexpr int WC = croft_col_width(N, 8, true);
+        constexpr int WC = croft_col_width(N, 8);
         const int c = threadIdx.x % WC;
         const int lane = threadIdx.x / WC;
         const long long col = tile * WC + c;

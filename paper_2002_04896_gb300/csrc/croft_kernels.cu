@@ -12,15 +12,12 @@
 
 namespace croft {
 
-// COL kernels exist for the two tile widths the planner can pick (croft_col_width with
-// close or distant rows; one kernel when they agree).  w: the width asked for.
+// One COL kernel per length: tile width croft_col_width, launch bound croft_col_minb.
+// w: the width asked for (a kernel exists only for that one).
 template <int N>
 static pass_fn col_kernel(int w) {
-    constexpr int W_NEAR = croft_col_width(N, 8, true);
-    constexpr int W_FAR = croft_col_width(N, 8, false);
-    if (w == W_FAR) return croft_pass_kernel<LAYOUT_COL, N, float2, W_FAR>;
-    if (w == W_NEAR) return croft_pass_kernel<LAYOUT_COL, N, float2, W_NEAR>;
-    return nullptr;
+    constexpr int W = croft_col_width(N, 8);
+    return w == W ? croft_pass_kernel<LAYOUT_COL, N, float2, W, croft_col_minb(N, 8)> : nullptr;
 }
 
 pass_fn CROFT_CAT(lookup_pass_kernel_group_, CROFT_GROUP)(int layout, int n, int w) {

@@ -11,10 +11,9 @@
 
 namespace croft {
 
-// (complex128 COL tiles take one width whatever the stride: croft_col_width(N, 16, *))
 template <int N>
 static pass64_fn col64_kernel(int w) {
-    constexpr int W = croft_col_width(N, 16, false);
+    constexpr int W = croft_col_width(N, 16);
     return (w == W || w == 0) ? croft_pass_kernel<LAYOUT_COL, N, double2, W> : nullptr;
 }
 

@@ -29,8 +29,9 @@ namespace croft {
 // (complex64, the default) or double2 (complex128, twiddles from A.tw64).
 // COL kernels are specialised on the column-tile width WC as well (so the
 // shared-memory indices fold into constants); ROW kernels take W from A.W.
-template <int LAYOUT, int N, class C = float2, int WC = 0>
-__global__ void __launch_bounds__(512) croft_pass_kernel(const C* in, C* out, const __grid_constant__ PassArgs A) {
+// MINB: CTAs per SM the register allocation must allow (launch bound).
+template <int LAYOUT, int N, class C = float2, int WC = 0, int MINB = 1>
+__global__ void __launch_bounds__(512, MINB) croft_pass_kernel(const C* in, C* out, const __grid_constant__ PassArgs A) {
     constexpr int T = croft_threads_per_pencil(N);
     extern __shared__ __align__(16) unsigned char smem_raw[];
     C* smem = reinterpret_cast<C*>(smem_raw);

@@ -115,15 +115,6 @@ std::string batch_describe(const croft_plan_s* p);
 
 static int g_max_smem = 0;
 
-// Tuning override of the column-tile width: the first of the named variables that is set (0: none).
-static int env_width(const char* a, const char* b = nullptr) {
-    for (const char* k : {a, b}) {
-        if (!k) continue;
-        const char* v = getenv(k);
-        if (v && atoi(v) >= 1) return atoi(v);
-    }
-    return 0;
-}
 
 // Launch shape of one pass (layouts: croft_internal.h; kernel: croft_pass_kernel.cuh).
 // ROW: W pencils of length n per CTA, each padded to n + n/16 + 1 slots.
@@ -159,7 +150,7 @@ static bool shape_pass(PassLaunch& L, int layout, int n, long long M, long long 
         if (tc) {
             while (W * 2 * T <= 256) W *= 2;
         } else {
-            W = croft_col_width(n, (int)es, M * es <= 64 * 1024);  // the width the kernels are built for
+            W = croft_col_width(n, (int)es);  // the width the kernels are built for
         }
         if (want_w >= 1 && !tc) W = want_w;
         while (W > 1 && (W * T > max_threads || (A.tw_pad + (long long)n * W) * es > smem_cap)) W /= 2;
@@ -312,10 +303,7 @@ static croft_status add_axis_pass(croft_plan p, int axis, int x0 = 0, int nxs = 
         }
     }
     PassLaunch L;
-    // (tuning override of the COL tile width; honoured only for a width a kernel is built for)
-    int want_w = layout == LAYOUT_COL ? env_width(axis == 1 ? "CROFT_COL_W_Y" : "CROFT_COL_W_X", "CROFT_COL_W") : 0;
-    if (want_w && (f64 ? !pass64_kernel_for(layout, n, want_w) : !pass_kernel_for(layout, n, want_w))) want_w = 0;
-    if (!shape_pass(L, layout, n, M, N / n, p->axis_tc[axis], f64, want_w)) return CROFT_ERR_UNSUPPORTED_SIZE;
+    if (!shape_pass(L, layout, n, M, N / n, p->axis_tc[axis], f64)) return CROFT_ERR_UNSUPPORTED_SIZE;
     L.kind = PASS_AXIS;
     L.args.tw = p->tw_dev[axis];
     L.args.tw64 = f64 ? (const double2*)p->tw_dev[axis] : nullptr;

@@ -95,26 +95,31 @@ CROFT_HD constexpr int croft_threads_per_pencil(int n) {
 }
 
 // Column-tile width (columns per CTA) of a COL pass - a compile-time constant of
-// its kernel - for length n, complex element size es bytes, and whether the rows
-// of a pencil are close in memory (axis stride of at most 64 KB).  16 columns
-// (128-byte rows), widened while the CTA stays within 256 threads.  Complex64
-// pencils of 32 threads (lengths of a few hundred) take 8 columns when the rows
-// are close: 256-thread CTAs, four per SM instead of two 512-thread ones by
-// registers (y pass of 480^3: 457 -> 409 us); across long strides the 64-byte
-// row segments cost more than the occupancy gains (x pass of 480^3: 463 -> 514
-// us), so 16 stays.  Narrowed while the CTA exceeds 512 threads or the data tile
-// 100 KB.
-CROFT_HD constexpr int croft_col_width(int n, int es, bool near_rows) {
+// its kernel - for length n and complex element size es bytes: 16 columns
+// (128-byte rows), widened while the CTA stays within 256 threads, narrowed while
+// the CTA exceeds 512 threads or the data tile 100 KB.  (A strided-copy probe
+// with the same tiles reaches 0.97 of the copy peak across the x pass's
+// megabyte strides with 16 columns and 0.47 with 8.)
+CROFT_HD constexpr int croft_col_width(int n, int es) {
     const int t = croft_threads_per_pencil(n);
     int w = 16;
     while (w * 2 * t <= 256) w *= 2;
-    if (es == 8 && t == 32 && near_rows) w = 8;
     const long long tw_pad = ((n + 1) / 2) * 2;
     while (w > 1 && (w * t > 512 || (tw_pad + (long long)n * w) * es > 100 * 1024)) w /= 2;
     return w;
 }
 
-// Column-tile width of the fused convolution pass: the near-rows width whatever the
-// stride - that pass does twice the arithmetic per byte, so occupancy matters more
-// (480^3: 927 -> 801 us with 8 columns).
-CROFT_HD constexpr int croft_conv_width(int n, int es) { return croft_col_width(n, es, true); }
+// CTAs per SM that a COL pass kernel's register allocation must allow (its launch
+// bound).  Complex64 pencils of 32 threads (lengths 270..512) make 512-thread
+// CTAs that take ~60 registers unconstrained - two per SM, and the compute phase
+// of both can leave no loads in flight; bounding them to three per SM (40
+// registers, 12-44 bytes of spills) measured 15-37 % faster on the y and x passes
+// of 320^3 .. 512^3 grids.
+CROFT_HD constexpr int croft_col_minb(int n, int es) { return (es == 8 && croft_threads_per_pencil(n) == 32) ? 3 : 1; }
+
+// Column-tile width of the fused convolution pass: as croft_col_width, but 8 columns
+// for complex64 pencils of 32 threads (four 256-thread CTAs per SM; the fused pass
+// does twice the arithmetic per byte, so occupancy matters more: 480^3 927 -> 801 us).
+CROFT_HD constexpr int croft_conv_width(int n, int es) {
+    return (es == 8 && croft_threads_per_pencil(n) == 32) ? 8 : croft_col_width(n, es);
+}
