@@ -51,17 +51,17 @@ __device__ __forceinline__ void conv_cp_async(R* dst_smem, const R* src) {
 // constant, so every shared-memory index folds into constants).  For complex64
 // power-of-two lengths with 16-thread pencils (W = 16, 256-thread CTAs), asking
 // for four CTAs per SM keeps the kernel at 64 registers (72 at N = 256
-// otherwise: three CTAs per SM).  Complex64 pencils of 32 threads take the COL
-// passes' bound of three 512-thread CTAs per SM (croft_col_minb).  Other lengths
-// keep the 128-register bound: radix-3/5 stages and complex128 spill at 64.
+// otherwise: three CTAs per SM).  Complex64 pencils of 32 threads make 512-thread
+// CTAs whose tiles (data + G, ~100 KB at N = 512) allow two per SM, so they are
+// bound to two (64 registers).  Other lengths keep the 128-register bound:
+// radix-3/5 stages and complex128 spill at 64.
 template <int N, class C>
 struct ConvShape {
     static constexpr int T = croft_threads_per_pencil(N);
     static constexpr int W = croft_conv_width(N, (int)sizeof(C));
     static constexpr int THREADS = W * T;
     static constexpr bool TIGHT = sizeof(C) == 8 && THREADS == 256 && T <= 16 && (N & (N - 1)) == 0;
-    static constexpr int MIN_BLOCKS =
-        TIGHT ? 4 : (croft_col_minb(N, (int)sizeof(C)) > 1 ? croft_col_minb(N, (int)sizeof(C)) : (THREADS <= 256 ? 2 : 1));
+    static constexpr int MIN_BLOCKS = TIGHT ? 4 : (THREADS <= 256 || (sizeof(C) == 8 && T == 32) ? 2 : 1);
 };
 
 // Shared memory: [twiddles: tw_pad][tile: N x W complex][G tile: N x W real].

@@ -117,7 +117,6 @@ CROFT_HD constexpr int croft_col_width(int n, int es) {
 // of 320^3 .. 512^3 grids.
 CROFT_HD constexpr int croft_col_minb(int n, int es) { return (es == 8 && croft_threads_per_pencil(n) == 32) ? 3 : 1; }
 
-// Column-tile width of the fused convolution pass: the same as a COL pass (with the
-// same three-CTAs-per-SM bound for 32-thread pencils; 8 columns measured slower at
-// every size from 384 to 512: 480^3 774 vs 690 us).
+// Column-tile width of the fused convolution pass: the same as a COL pass (8 columns
+// measured slower at every size from 384 to 512: 480^3 774 vs 690 us).
 CROFT_HD constexpr int croft_conv_width(int n, int es) { return croft_col_width(n, es); }
