@@ -11,7 +11,7 @@
 namespace croft {
 
 #define CROFT_CONV_CASE(N) \
-    case N: return croft_conv_kernel<N, float2>;
+    case N: return conv_kernel_of<N, float2>();
 
 #define CROFT_CAT_(a, b) a##b
 #define CROFT_CAT(a, b) CROFT_CAT_(a, b)
@@ -27,7 +27,7 @@ conv_fn CROFT_CAT(lookup_conv_kernel_group_, CROFT_CONV_GROUP)(int n) {
 // complex128: the lengths of the complex128 pass kernels
 conv64_fn conv64_kernel_for(int n) {
 #define CROFT_CONV64_CASE(N) \
-    case N: return croft_conv_kernel<N, double2>;
+    case N: return conv_kernel_of<N, double2>();
     switch (n) {
         CROFT_SIZES64(CROFT_CONV64_CASE)
         default: return nullptr;

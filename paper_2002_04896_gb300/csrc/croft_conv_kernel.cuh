@@ -61,13 +61,14 @@ struct ConvShape {
     static constexpr int W = croft_conv_width(N, (int)sizeof(C));
     static constexpr int THREADS = W * T;
     static constexpr bool TIGHT = sizeof(C) == 8 && THREADS == 256 && T <= 16 && (N & (N - 1)) == 0;
-    static constexpr int MIN_BLOCKS = TIGHT ? 4 : (THREADS <= 256 || (sizeof(C) == 8 && T == 32) ? 2 : 1);
+    // 0: no minimum in the launch bound (an explicit minimum of one or two lets ptxas
+    // take far more registers than it does without one)
+    static constexpr int MIN_BLOCKS = TIGHT ? 4 : ((sizeof(C) == 8 && T == 32) ? 2 : 0);
 };
 
 // Shared memory: [twiddles: tw_pad][tile: N x W complex][G tile: N x W real].
-template <int N, class C = float2>
-__global__ void __launch_bounds__(ConvShape<N, C>::THREADS, ConvShape<N, C>::MIN_BLOCKS)
-    croft_conv_kernel(const C* in, C* out, const typename CxScalar<C>::T* g, const __grid_constant__ PassArgs A) {
+template <int N, class C>
+__device__ __forceinline__ void conv_body(const C* in, C* out, const typename CxScalar<C>::T* g, const PassArgs& A) {
     using R = typename CxScalar<C>::T;
     constexpr int T = ConvShape<N, C>::T;
     constexpr int W = ConvShape<N, C>::W;
@@ -123,6 +124,25 @@ __global__ void __launch_bounds__(ConvShape<N, C>::THREADS, ConvShape<N, C>::MIN
         smem_stages<N, 1, sc.count - 1, T>(work, stw, lane, ok);
         fft_stage<N, sc.count - 1, T>(work, NoBarrier{}, dst, stw, lane, ok);
     }
+}
+
+template <int N, class C = float2>
+__global__ void __launch_bounds__(ConvShape<N, C>::THREADS)
+    croft_conv_kernel(const C* in, C* out, const typename CxScalar<C>::T* g, const __grid_constant__ PassArgs A) {
+    conv_body<N, C>(in, out, g, A);
+}
+
+template <int N, class C = float2>
+__global__ void __launch_bounds__(ConvShape<N, C>::THREADS, ConvShape<N, C>::MIN_BLOCKS > 0 ? ConvShape<N, C>::MIN_BLOCKS : 1)
+    croft_conv_kernel_bounded(const C* in, C* out, const typename CxScalar<C>::T* g, const __grid_constant__ PassArgs A) {
+    conv_body<N, C>(in, out, g, A);
+}
+
+// The kernel of length N: bounded when ConvShape asks for a minimum of CTAs per SM.
+template <int N, class C>
+constexpr auto conv_kernel_of() {
+    if constexpr (ConvShape<N, C>::MIN_BLOCKS > 0) return croft_conv_kernel_bounded<N, C>;
+    else return croft_conv_kernel<N, C>;
 }
 
 // out[i] = in[i] * g[i] (the multiply on its own, for plans whose last pass cannot

@@ -17,7 +17,9 @@ namespace croft {
 template <int N>
 static pass_fn col_kernel(int w) {
     constexpr int W = croft_col_width(N, 8);
-    return w == W ? croft_pass_kernel<LAYOUT_COL, N, float2, W, croft_col_minb(N, 8)> : nullptr;
+    if (w != W) return nullptr;
+    if constexpr (croft_col_minb(N, 8) > 1) return croft_pass_kernel_bounded<LAYOUT_COL, N, float2, W, croft_col_minb(N, 8)>;
+    else return croft_pass_kernel<LAYOUT_COL, N, float2, W>;
 }
 
 pass_fn CROFT_CAT(lookup_pass_kernel_group_, CROFT_GROUP)(int layout, int n, int w) {

@@ -29,9 +29,8 @@ namespace croft {
 // (complex64, the default) or double2 (complex128, twiddles from A.tw64).
 // COL kernels are specialised on the column-tile width WC as well (so the
 // shared-memory indices fold into constants); ROW kernels take W from A.W.
-// MINB: CTAs per SM the register allocation must allow (launch bound).
-template <int LAYOUT, int N, class C = float2, int WC = 0, int MINB = 1>
-__global__ void __launch_bounds__(512, MINB) croft_pass_kernel(const C* in, C* out, const __grid_constant__ PassArgs A) {
+template <int LAYOUT, int N, class C, int WC>
+__device__ __forceinline__ void pass_body(const C* in, C* out, const PassArgs& A) {
     constexpr int T = croft_threads_per_pencil(N);
     extern __shared__ __align__(16) unsigned char smem_raw[];
     C* smem = reinterpret_cast<C*>(smem_raw);
@@ -65,6 +64,21 @@ __global__ void __launch_bounds__(512, MINB) croft_pass_kernel(const C* in, C* o
         fft_pencil<N, T>(GlobalInT<C>{in + base, A.M, A.isign}, SmemColFixed<C, (WC > 0 ? WC : 1)>{sbuf + c},
                          GlobalOutT<C>{out + base, A.M, A.isign}, stw, lane, ok);
     }
+}
+
+// The pass kernel.  (Its launch bound names no minimum of CTAs per SM: with an
+// explicit minimum of one, ptxas allocates far more registers - 83 instead of 52
+// for the 256-point COL kernel - and the pass slows from 46 to 60 us.)
+template <int LAYOUT, int N, class C = float2, int WC = 0>
+__global__ void __launch_bounds__(512) croft_pass_kernel(const C* in, C* out, const __grid_constant__ PassArgs A) {
+    pass_body<LAYOUT, N, C, WC>(in, out, A);
+}
+
+// The same with registers bounded for MINB CTAs of 512 threads per SM (croft_col_minb).
+template <int LAYOUT, int N, class C, int WC, int MINB>
+__global__ void __launch_bounds__(512, MINB) croft_pass_kernel_bounded(const C* in, C* out,
+                                                                        const __grid_constant__ PassArgs A) {
+    pass_body<LAYOUT, N, C, WC>(in, out, A);
 }
 
 }  // namespace croft
