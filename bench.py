@@ -147,6 +147,23 @@ def dist_env():
     return world, rank, local
 
 
+def max_over_ranks(torch, value: float, device) -> float:
+    """The largest of every rank's `value` (an all-reduce, so also a barrier); `value` itself
+    when no process group is initialised.  Times are aggregated this way: the job takes as
+    long as its slowest rank."""
+    dist = torch.distributed
+    if not (dist.is_available() and dist.is_initialized()):
+        return value
+    t = torch.tensor([value], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_gflops(world: int, flops_per_rank_step: float, ms_step: float) -> float:
+    """Whole-job throughput: every rank runs its own replica of the step (weak scaling)."""
+    return world * flops_per_rank_step / (ms_step * 1e-3) / 1e9
+
+
 def cpu_oracle_step(x, sample_planes=None):
     """Forward + backward with the FP64 oracle; optionally on a sample of the pencils of each axis.
 
@@ -514,14 +531,9 @@ def run_croft(args):
         step_per_pass(rec_pp)
     croft.croft_plan_set_timing(plan.handle, False)
     clk = clocks.stop()
-    ms_total = sum(rec)
-    if world > 1:
-        t = torch.tensor([ms_total], device=dev)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        ms_total = float(t.item())
-        torch.distributed.barrier()
+    ms_total = max_over_ranks(torch, sum(rec), dev)
     ms_step = ms_total / args.steps
-    value = world * flops_step / (ms_step * 1e-3) / 1e9
+    value = job_gflops(world, flops_step, ms_step)
 
     # per-pass kernel times (forward and backward run the same kernels)
     npass = len(rec_pp[0][0])
@@ -574,11 +586,8 @@ def run_croft(args):
         if i >= args.warmup:
             e2e_serial.append(a.elapsed_time(b))
     e2e_serial_ms = statistics.mean(e2e_serial)
-    if world > 1:
-        t = torch.tensor([e2e_ms], device=dev)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        e2e_ms = float(t.item())
-    e2e_val = world * flops_step / (e2e_ms * 1e-3) / 1e9
+    e2e_ms = max_over_ranks(torch, e2e_ms, dev)
+    e2e_val = job_gflops(world, flops_step, e2e_ms)
     zr = z_pin.numpy().astype(np.complex128)
     xr = x_h.astype(np.complex128) * n_total
     e2e_check = float(np.linalg.norm(zr - xr) / np.linalg.norm(xr))
@@ -634,7 +643,7 @@ def run_croft(args):
                            "steps overlapped on three streams)",
                     "roundtrip_rel_l2": e2e_check,
                     "serialised_ms_per_step": e2e_serial_ms,
-                    "serialised_value": world * flops_step / (e2e_serial_ms * 1e-3) / 1e9},
+                    "serialised_value": job_gflops(world, flops_step, e2e_serial_ms)},
             "gpu_launches": launches_per_step * args.steps,
             "gpu_launches_note": "croft kernels inside the device-timed steps (the e2e region launches the same per step)",
             "rows": rows,
