@@ -61,7 +61,7 @@ def measured_peaks():
 # The sources that decide the pass kernels' code and launch shape: a DRAM-traffic figure
 # taken with ncu stays valid while these files are unchanged.
 PASS_KERNEL_SOURCES = ("croft_butterflies.cuh", "croft_fft_core.cuh", "croft_internal.h", "croft_kernels.cu",
-                       "croft_pass_kernel.cuh", "croft_passes.cu", "croft_plan.cu", "croft_row_layouts.h",
+                       "croft_pass_kernel.cuh", "croft_passes.cu", "croft_row_layouts.h",
                        "croft_sched.h", "croft_sizes.h")
 
 

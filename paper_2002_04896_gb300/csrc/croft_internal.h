@@ -125,6 +125,10 @@ cudaError_t launch_scale(const void* in, void* out, const void* g, long long n, 
                          bool pdl = false);
 
 // croft_passes.cu
+extern int g_max_smem;  // the device's opt-in shared memory per block (set by plan creation)
+// Launch shape of one axis pass (tile width, block, grid, shared memory); false when no shape fits.
+bool shape_pass(PassLaunch& L, int layout, int n, long long M, long long ncols, bool tc = false, bool f64 = false,
+                int want_w = 0);
 pass_fn pass_kernel_for(int layout, int n, int w);
 conv_fn conv_kernel_for(int n);
 pipe_fn pipe_kernel_for(int layout, int n);

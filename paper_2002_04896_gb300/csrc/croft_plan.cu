@@ -113,61 +113,7 @@ int batch_num_launches(const croft_plan_s* p);
 std::string batch_describe(const croft_plan_s* p);
 }  // namespace croft
 
-static int g_max_smem = 0;
-
-
-// Launch shape of one pass (layouts: croft_internal.h; kernel: croft_pass_kernel.cuh).
-// ROW: W pencils of length n per CTA, each padded to n + n/16 + 1 slots.
-// COL: W adjacent columns per CTA, W a multiple of 16 (128-byte rows).
-// Aim for ~256 threads per CTA and <= 100 KB of shared memory so that at
-// least two CTAs share an SM.
-static bool shape_pass(PassLaunch& L, int layout, int n, long long M, long long ncols, bool tc = false,
-                       bool f64 = false, int want_w = 0) {
-    memset(&L, 0, sizeof(L));
-    L.layout = layout;
-    L.tc = tc ? 1 : 0;
-    L.f64 = f64 ? 1 : 0;
-    const long long es = f64 ? 16 : 8;  // bytes per element
-    PassArgs& A = L.args;
-    A.n = n;
-    A.M = M;
-    A.ncols = ncols;
-    const int T = croft_threads_per_pencil(n);
-    L.T = T;
-    A.tw_pad = ((n + 1) / 2) * 2;  // keeps the tile 16-byte aligned
-    const long long smem_cap = 100 * 1024;
-    const int max_threads = 512;   // the kernels' launch bound
-    if (layout == LAYOUT_ROW) {
-        const int ld = tc ? croft_row_ld(n) : croft_row_ld_staged(n);
-        int W = (256 + T - 1) / T;
-        if (W < 1) W = 1;
-        while (W > 1 && (W * T > max_threads || (A.tw_pad + (long long)W * ld) * es > smem_cap)) --W;
-        if ((long long)W > ncols && !tc) W = (int)ncols;  // (tensor-core tiles keep whole 128-row groups)
-        A.W = W;
-        L.smem = (int)((A.tw_pad + (long long)W * ld) * es);
-    } else {
-        int W = 16;
-        if (tc) {
-            while (W * 2 * T <= 256) W *= 2;
-        } else {
-            W = croft_col_width(n, (int)es);  // the width the kernels are built for
-        }
-        if (want_w >= 1 && !tc) W = want_w;
-        while (W > 1 && (W * T > max_threads || (A.tw_pad + (long long)n * W) * es > smem_cap)) W /= 2;
-        A.W = W;
-        L.smem = (int)((A.tw_pad + (long long)n * W) * es);
-    }
-    if (croft_make_sched(n).count <= 1 && !tc) L.smem = 0;  // single-stage kernels touch no shared memory
-    if (tc) L.smem += 4096;                                  // + the DFT-16 operand
-    L.block = A.W * T;
-    if (tc && (L.block % 128) != 0) return false;           // 128-butterfly GEMM groups
-    if (L.block > max_threads) return false;
-    long long grid = (ncols + A.W - 1) / A.W;
-    if (grid > 0x7fffffffLL) return false;
-    L.grid = (int)grid;
-    if (L.smem > g_max_smem) return false;
-    return true;
-}
+// (shape_pass and the device's shared-memory limit g_max_smem live in croft_passes.cu)
 
 // Launch shape of a TMA-pipelined persistent pass (croft_pipe_kernel.cuh): two tile
 // buffers per CTA, 128-byte aligned; as many resident CTAs as fit, capped by the tiles.
