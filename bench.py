@@ -440,6 +440,48 @@ def measure_rows(croft, torch, dev, stream, flush, peak, only=None):  # noqa: PL
     return rows
 
 
+def library_context(torch, x, flush, stream, x_h, flops_step, skip_cpu):
+    """cuFFT (torch.fft.fftn / ifftn, both unnormalised) forward+backward on the device grid, timed
+    like the croft steps (L2 flushed, events at the ends); scipy.fft on the host cores."""
+    out = {}
+    times = []
+    for i in range(8):
+        with torch.cuda.stream(stream):
+            _flush(flush)
+            a = torch.cuda.Event(enable_timing=True)
+            b = torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            yf = torch.fft.fftn(x, norm="backward")
+            torch.fft.ifftn(yf, norm="forward")
+            b.record(stream)
+        stream.synchronize()
+        if i >= 3:
+            times.append(a.elapsed_time(b))
+    ms = statistics.median(times)
+    out["cufft_torch_fftn"] = {"ms_per_step": ms, "gflops": flops_step / (ms * 1e-3) / 1e9,
+                               "note": "torch.fft.fftn + ifftn(norm='forward') on the same 256^3 complex64 grid"}
+    if not skip_cpu:
+        try:
+            import numpy as np
+            import scipy.fft as sfft
+            for name, dt in (("complex64", np.complex64), ("complex128", np.complex128)):
+                xc = x_h.astype(dt)
+                sfft.ifftn(sfft.fftn(xc, workers=os.cpu_count()), norm="forward", workers=os.cpu_count())
+                t0 = time.perf_counter()
+                reps = 0
+                while True:
+                    sfft.ifftn(sfft.fftn(xc, workers=os.cpu_count()), norm="forward", workers=os.cpu_count())
+                    reps += 1
+                    if time.perf_counter() - t0 > 3.0:
+                        break
+                sec = (time.perf_counter() - t0) / reps
+                out[f"scipy_fft_{name}"] = {"ms_per_step": sec * 1e3, "gflops": flops_step / sec / 1e9,
+                                             "cores": os.cpu_count()}
+        except Exception as e:  # noqa: BLE001 - context only
+            out["scipy_fft"] = {"unavailable": str(e)[:200]}
+    return out
+
+
 def run_croft(args):
     import numpy as np
     import torch
@@ -617,6 +659,12 @@ def run_croft(args):
                "sample": f"FP64 oracle (numpy matmul per-axis DFT), {reps} full forward+backward step(s) of the "
                          f"pme256 grid in {dt:.1f} s"}
 
+    # library context (not targets, not oracles): cuFFT through torch.fft on the same grid and
+    # protocol, and a multi-threaded CPU FFT (scipy's pocketfft) on the host cores
+    context = None
+    if rank == 0 and not args.no_rows:
+        context = library_context(torch, x, flush, stream, x_h, flops_step, args.no_cpu_baseline)
+
     plan.close()
     if rank == 0:
         line = {
@@ -642,6 +690,7 @@ def run_croft(args):
                                           "is the same figure from the per-pass events alone)"},
             "hbm_frac_whole_transform": (16.0 * n_total * 2 / (ms_step * 1e-3) / 1e9) / peak,
             "cpu_baseline": cpu,
+            "library_context": context,
             "e2e": {"value": e2e_val, "unit": "GFLOP/s", "h2d_bytes_per_step": 8 * n_total,
                     "d2h_bytes_per_step": 8 * n_total, "ms_per_step": e2e_ms,
                     "api": "croft_exec_host_pipeline (upload, forward, backward, download per step; "
