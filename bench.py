@@ -320,13 +320,21 @@ def measure_rows(croft, torch, dev, stream, flush, peak, only=None):  # noqa: PL
         stream.synchronize()
         rt = float(torch.linalg.vector_norm((z - n * x).flatten()) / torch.linalg.vector_norm((n * x).flatten()))
         t = f_ms + b_ms
+        cufft = None
+        if dtype == 0:  # library context: cuFFT through torch.fft, same protocol
+            del z
+            cf, cb, _ = time_transform(croft, torch, stream, flush, None,
+                                       lambda: torch.fft.fftn(x, norm="backward", out=y),
+                                       lambda: torch.fft.ifftn(y, norm="forward"))
+            cufft = {"ms_fwd": cf, "ms_bwd": cb, "gflops": 2 * nominal_flops(shape) / ((cf + cb) * 1e-3) / 1e9}
+            z = None
         dom = max(range(len(pass_ms)), key=lambda i: pass_ms[i])
         rows[name] = {"shape": list(shape), "ms_fwd": f_ms, "ms_bwd": b_ms,
                       "gflops": 2 * nominal_flops(shape) / (t * 1e-3) / 1e9,
                       "hbm_frac_whole_transform": (32.0 * n / (t * 1e-3) / 1e9) / peak,
                       "pass_ms": pass_ms, "dominant_pass_gbs": 16.0 * n / (pass_ms[dom] * 1e-3) / 1e9,
                       "dominant_pass_frac": (16.0 * n / (pass_ms[dom] * 1e-3) / 1e9) / peak,
-                      "roundtrip_rel_l2": rt, "plan": desc}
+                      "roundtrip_rel_l2": rt, "plan": desc, "cufft_torch_fftn_context": cufft}
         del x, y, z
     if want("pme256_convolve"):
         # PME reciprocal-space convolution B(G * F(x)) on 256^3 with the smooth-PME influence function:
