@@ -641,6 +641,29 @@ def run_croft(args):
         if i >= args.warmup:
             e2e_serial.append(a.elapsed_time(b))
     e2e_serial_ms = statistics.mean(e2e_serial)
+    # the host link's own rate for this traffic: one step's upload and download at once, on two
+    # streams, copy engines only (the pipelined e2e step cannot beat it)
+    s2 = torch.cuda.Stream(device=dev)
+    link = []
+    for i in range(5):
+        with torch.cuda.stream(stream):
+            a = torch.cuda.Event(enable_timing=True)
+            b = torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            s2.wait_event(a)
+            x.copy_(x_pin, non_blocking=True)
+        with torch.cuda.stream(s2):
+            z_pin.copy_(z, non_blocking=True)
+            c = torch.cuda.Event()
+            c.record(s2)
+        with torch.cuda.stream(stream):
+            stream.wait_event(c)
+            b.record(stream)
+        stream.synchronize()
+        if i >= 1:
+            link.append(a.elapsed_time(b))
+    link_ms = statistics.median(link)
+    link_gbs = 16.0 * n_total / (link_ms * 1e-3) / 1e9
     e2e_ms = max_over_ranks(torch, e2e_ms, dev)
     e2e_val = job_gflops(world, flops_step, e2e_ms)
     zr = z_pin.numpy().astype(np.complex128)
@@ -705,7 +728,11 @@ def run_croft(args):
                            "steps overlapped on three streams)",
                     "roundtrip_rel_l2": e2e_check,
                     "serialised_ms_per_step": e2e_serial_ms,
-                    "serialised_value": job_gflops(world, flops_step, e2e_serial_ms)},
+                    "serialised_value": job_gflops(world, flops_step, e2e_serial_ms),
+                    "link_roofline": {"bound": "host link", "achieved_gbs": 16.0 * n_total / (e2e_ms * 1e-3) / 1e9,
+                                      "peak_gbs": link_gbs, "frac": link_ms / e2e_ms,
+                                      "peak_source": "this step's upload and download copied at once on two "
+                                                     "streams, measured here"}},
             "gpu_launches": launches_per_step * args.steps,
             "gpu_launches_note": "croft kernels inside the device-timed steps (the e2e region launches the same per step)",
             "rows": rows,
