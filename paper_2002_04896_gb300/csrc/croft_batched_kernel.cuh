@@ -93,7 +93,7 @@ __device__ __noinline__ void batch_tile(const BatchGrid& G, int pass, int tile, 
         const long long col = (long long)tile * W + c;
         const bool ok = lane < T && col < G.ncols[pass];
         const long long cc = ok ? col : 0;
-        const long long b = col_div(cc, M);
+        const long long b = cc / M;
         const long long m = cc - b * M;
         const long long base = b * (long long)N * M + m;
         fft_pencil<N, T>(GlobalInCG{in + base, M, isign}, SmemCol{sbuf + c, W},

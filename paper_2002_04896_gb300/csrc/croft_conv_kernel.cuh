@@ -85,7 +85,7 @@ __device__ __forceinline__ void conv_body(const C* in, C* out, const typename Cx
     const int lane = threadIdx.x / W;
     const long long col = (long long)blockIdx.x * W + c;
     const bool ok = col < A.ncols;
-    const long long b = col_div(col, A.M);
+    const long long b = col / A.M;
     const long long m = col - b * A.M;
     const long long base = b * (long long)N * A.M + m;
 

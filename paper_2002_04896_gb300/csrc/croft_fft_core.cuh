@@ -127,14 +127,6 @@ struct SmemColFixed {
     __device__ __forceinline__ void store(int a, C v) const { s[a * W] = v; }
 };
 
-// q = x / d for the column-to-pencil-row split of a COL pass (x, d >= 1): a 32-bit
-// division when both fit (a 64-bit division is a ~70-instruction subroutine, paid by
-// every thread of every column pass), else 64-bit.
-__device__ __forceinline__ long long col_div(long long x, long long d) {
-    if (((unsigned long long)x | (unsigned long long)d) <= 0xffffffffULL) return (long long)((unsigned)x / (unsigned)d);
-    return x / d;
-}
-
 // ---------------------------------------------------------------------------
 // programmatic dependent launch
 // ---------------------------------------------------------------------------

@@ -58,7 +58,7 @@ __global__ void __launch_bounds__(256) croft_group_kernel(const __grid_constant_
         const int lane = threadIdx.x / WC;
         const long long col = tile * WC + c;
         const bool ok = col < S.ncols;
-        const long long b = col_div(col, S.M);
+        const long long b = col / S.M;
         const long long m = col - b * S.M;
         const long long base = b * (long long)N * S.M + m;
         fft_pencil<N, T>(GlobalIn{S.in + base, S.M, A.isign}, SmemColFixed<float2, WC>{sbuf + c},

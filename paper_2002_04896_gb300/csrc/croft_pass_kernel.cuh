@@ -58,7 +58,7 @@ __device__ __forceinline__ void pass_body(const C* in, C* out, const PassArgs& A
         const int lane = threadIdx.x / WC;
         const long long col = (long long)blockIdx.x * WC + c;
         const bool ok = col < A.ncols;
-        const long long b = col_div(col, A.M);
+        const long long b = col / A.M;
         const long long m = col - b * A.M;
         const long long base = b * (long long)N * A.M + m;
         fft_pencil<N, T>(GlobalInT<C>{in + base, A.M, A.isign}, SmemColFixed<C, (WC > 0 ? WC : 1)>{sbuf + c},

@@ -284,7 +284,7 @@ __global__ void __launch_bounds__(512) croft_pass_kernel_tc(const float2* in, fl
         ok = col < A.ncols;
         M = A.M;
         const long long cc = ok ? col : 0;
-        const long long b = col_div(cc, M);
+        const long long b = cc / M;
         const long long m = cc - b * M;
         base = b * (long long)N * M + m;
     }
