@@ -6,8 +6,8 @@
 // transform reuses them through conj(F(conj(x))), applied at the global load
 // and store of each pass.
 //
-// Radix 8 and 16 are split Cooley-Tukey (2x4 and 4x4) with the inner twiddles
-// as compile-time constants; 3 and 5 use the symmetric cos/sin form.  The
+// Radix 8, 9, 15 and 16 are split Cooley-Tukey (2x4, 3x3, 5x3 and 4x4) with the
+// inner twiddles as compile-time constants; 3 and 5 use the symmetric cos/sin form.  The
 // constants are the exact mathematical values rounded to the working precision
 // (float for complex64, double for complex128).
 #pragma once
@@ -55,6 +55,22 @@ __device__ __forceinline__ C mul_cs(C a, typename CxScalar<C>::T c, typename CxS
 #define CROFT_C52 (-0.80901699437494742410)
 #define CROFT_S51 0.95105651629515357212
 #define CROFT_S52 0.58778525229247312917
+// cos and sin of 2 pi m / 9 (m = 1, 2, 4) and of 2 pi m / 15 (m = 1, 2, 4, 8; m = 3 and
+// 6 are the radix-5 constants above), exact values rounded to the working precision.
+#define CROFT_C9_1 0.7660444431189780352024
+#define CROFT_S9_1 0.6427876096865393263226
+#define CROFT_C9_2 0.1736481776669303488517
+#define CROFT_S9_2 0.9848077530122080593667
+#define CROFT_C9_4 (-0.9396926207859083840541)
+#define CROFT_S9_4 0.3420201433256687330441
+#define CROFT_C15_1 0.9135454576426008955021
+#define CROFT_S15_1 0.4067366430758002077540
+#define CROFT_C15_2 0.6691306063588582138263
+#define CROFT_S15_2 0.7431448254773942350147
+#define CROFT_C15_4 (-0.1045284632676534713998)
+#define CROFT_S15_4 0.9945218953682733369227
+#define CROFT_C15_8 (-0.9781476007338056379286)
+#define CROFT_S15_8 (-0.2079116908177593371017)
 
 template <int R, class C> __device__ __forceinline__ void dft(C* v);
 
@@ -169,6 +185,62 @@ template <class C> struct Dft<5, C> {
         v[4] = mkc<C>(a1.x - b1.y, a1.y + b1.x);
         v[2] = mkc<C>(a2.x + b2.y, a2.y - b2.x);
         v[3] = mkc<C>(a2.x - b2.y, a2.y + b2.x);
+    }
+};
+
+template <class C> struct Dft<9, C> {
+    __device__ __forceinline__ static void run(C* v) {
+        using T = typename CxScalar<C>::T;
+        // j = 3*j1 + j2: length-3 DFTs over j1, twiddle W9^(j2*k1), length-3 DFTs over j2.
+        C a[3][3];  // a[k1][j2]
+#pragma unroll
+        for (int j2 = 0; j2 < 3; ++j2) {
+            C t[3] = {v[j2], v[3 + j2], v[6 + j2]};
+            Dft<3, C>::run(t);
+            a[0][j2] = t[0];
+            a[1][j2] = t[1];
+            a[2][j2] = t[2];
+        }
+        a[1][1] = mul_cs(a[1][1], (T)CROFT_C9_1, -(T)CROFT_S9_1);  // W9^1
+        a[1][2] = mul_cs(a[1][2], (T)CROFT_C9_2, -(T)CROFT_S9_2);  // W9^2
+        a[2][1] = mul_cs(a[2][1], (T)CROFT_C9_2, -(T)CROFT_S9_2);  // W9^2
+        a[2][2] = mul_cs(a[2][2], (T)CROFT_C9_4, -(T)CROFT_S9_4);  // W9^4
+#pragma unroll
+        for (int k1 = 0; k1 < 3; ++k1) {
+            Dft<3, C>::run(a[k1]);
+#pragma unroll
+            for (int k2 = 0; k2 < 3; ++k2) v[k1 + 3 * k2] = a[k1][k2];
+        }
+    }
+};
+
+template <class C> struct Dft<15, C> {
+    __device__ __forceinline__ static void run(C* v) {
+        using T = typename CxScalar<C>::T;
+        // j = 3*j1 + j2 (j1 < 5, j2 < 3): length-5 DFTs over j1, twiddle W15^(j2*k1),
+        // length-3 DFTs over j2; output k1 + 5*k2.
+        C a[5][3];  // a[k1][j2]
+#pragma unroll
+        for (int j2 = 0; j2 < 3; ++j2) {
+            C t[5] = {v[j2], v[3 + j2], v[6 + j2], v[9 + j2], v[12 + j2]};
+            Dft<5, C>::run(t);
+#pragma unroll
+            for (int k1 = 0; k1 < 5; ++k1) a[k1][j2] = t[k1];
+        }
+        a[1][1] = mul_cs(a[1][1], (T)CROFT_C15_1, -(T)CROFT_S15_1);  // W15^1
+        a[2][1] = mul_cs(a[2][1], (T)CROFT_C15_2, -(T)CROFT_S15_2);  // W15^2
+        a[3][1] = mul_cs(a[3][1], (T)CROFT_C51, -(T)CROFT_S51);      // W15^3 = W5^1
+        a[4][1] = mul_cs(a[4][1], (T)CROFT_C15_4, -(T)CROFT_S15_4);  // W15^4
+        a[1][2] = mul_cs(a[1][2], (T)CROFT_C15_2, -(T)CROFT_S15_2);  // W15^2
+        a[2][2] = mul_cs(a[2][2], (T)CROFT_C15_4, -(T)CROFT_S15_4);  // W15^4
+        a[3][2] = mul_cs(a[3][2], (T)CROFT_C52, -(T)CROFT_S52);      // W15^6 = W5^2
+        a[4][2] = mul_cs(a[4][2], (T)CROFT_C15_8, -(T)CROFT_S15_8);  // W15^8
+#pragma unroll
+        for (int k1 = 0; k1 < 5; ++k1) {
+            Dft<3, C>::run(a[k1]);
+#pragma unroll
+            for (int k2 = 0; k2 < 3; ++k2) v[k1 + 5 * k2] = a[k1][k2];
+        }
     }
 };
 

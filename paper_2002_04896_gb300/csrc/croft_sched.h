@@ -19,8 +19,11 @@ struct CroftSched {
 };
 
 // Schedule: the power-of-two part of n in ceil(a/4) stages of (nearly) equal
-// size from {16, 8, 4, 2} (larger first), then one stage per factor 5 and per
-// factor 3.  The first stage needs no twiddles, so the largest radix goes there.
+// size from {16, 8, 4, 2} (larger first); then the odd part with the fewest
+// stages of at most 16 points: pairs of factors 3 as radix 9, an unpaired 3 with a
+// 5 as radix 15, then the remaining 5s and 3 (each stage is a shared-memory round
+// trip and a barrier).  The first stage needs no twiddles, so the largest radix
+// goes there.
 CROFT_HD constexpr CroftSched croft_make_sched(int n) {
     CroftSched s{0, {0, 0, 0, 0, 0, 0, 0, 0}};
     if (n < 1 || n > CROFT_MAX_N) {
@@ -41,8 +44,17 @@ CROFT_HD constexpr CroftSched croft_make_sched(int n) {
         const int base = a / st, extra = a % st;
         for (int i = 0; i < st; ++i) s.r[k++] = 1 << (base + (i < extra ? 1 : 0));
     }
+    const int n9 = c3 / 2;
+    int r3 = c3 % 2;
+    const int n15 = (r3 && c5 > 0) ? 1 : 0;
+    if (n15) {
+        r3 = 0;
+        c5 -= 1;
+    }
+    for (int i = 0; i < n15; ++i) s.r[k++] = 15;
+    for (int i = 0; i < n9; ++i) s.r[k++] = 9;
     for (int i = 0; i < c5; ++i) s.r[k++] = 5;
-    for (int i = 0; i < c3; ++i) s.r[k++] = 3;
+    for (int i = 0; i < r3; ++i) s.r[k++] = 3;
     s.count = k;
     return s;
 }

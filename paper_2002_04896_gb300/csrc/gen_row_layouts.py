@@ -46,7 +46,11 @@ def sched(n):
         st = (a + 3) // 4
         base, extra = a // st, a % st
         r += [1 << (base + (1 if i < extra else 0)) for i in range(st)]
-    return r + [5] * c5 + [3] * c3
+    n9, r3 = c3 // 2, c3 % 2  # must match croft_make_sched: 15, 9s, 5s, 3
+    n15 = 1 if (r3 and c5 > 0) else 0
+    if n15:
+        r3, c5 = 0, c5 - 1
+    return r + [15] * n15 + [9] * n9 + [5] * c5 + [3] * r3
 
 
 def emax(n):

@@ -81,7 +81,7 @@ def test_factorize_all_sizes(croft_lib):
             continue
         assert r is not None
         assert int(np.prod(r)) == n if r else n == 1
-        assert all(x in (2, 3, 4, 5, 8, 16) for x in r)
+        assert all(x in (2, 3, 4, 5, 8, 9, 15, 16) for x in r)
         assert len(r) <= 7
 
 
