@@ -50,7 +50,13 @@ def sched(n):
     n15 = 1 if (r3 and c5 > 0) else 0
     if n15:
         r3, c5 = 0, c5 - 1
-    return r + [15] * n15 + [9] * n9 + [5] * c5 + [3] * r3
+    r = sorted(r + [15] * n15 + [9] * n9 + [5] * c5 + [3] * r3, reverse=True)  # largest radix first ...
+    t = threads_per_pencil(n)  # ... but the first stage: the largest radix with <= emax elements per thread
+    for i, R in enumerate(r):
+        if -(-(n // R) // t) * R <= emax(n):
+            r = [R] + r[:i] + r[i + 1:]
+            break
+    return r
 
 
 def emax(n):

@@ -109,3 +109,16 @@ def test_twiddle_tables_match_float64_exponentials(croft_lib, n):
                     q = (4 * j * k) // (p * R)
                     assert tw[p - 1 + (j - 1) * p + k] == [1, -1j, -1, 1j][q % 4]
         p *= R
+
+
+def test_row_layout_generator_models_the_library_schedule(croft_lib):
+    """gen_row_layouts.py replays the kernels' stages: its schedule must be the library's, for every length."""
+    import importlib.util
+    import os
+    path = os.path.join(os.path.dirname(croft_lib.LIBRARY_PATH), "csrc", "gen_row_layouts.py")
+    spec = importlib.util.spec_from_file_location("gen_row_layouts", path)
+    gen = importlib.util.module_from_spec(spec)
+    spec.loader.exec_module(gen)
+    for n in range(2, 4097):
+        if gen.supported(n):
+            assert gen.sched(n) == croft_lib.croft_factorize(n), n
