@@ -42,10 +42,12 @@ def sched(n):
         m //= 5
         c5 += 1
     r = []
-    if a:
-        st = (a + 3) // 4
-        base, extra = a // st, a % st
-        r += [1 << (base + (1 if i < extra else 0)) for i in range(st)]
+    aa = a
+    while aa >= 4:
+        r.append(16)
+        aa -= 4
+    if aa:
+        r.append(1 << aa)
     n9, r3 = c3 // 2, c3 % 2  # must match croft_make_sched: 15, 9s, 5s, 3
     n15 = 1 if (r3 and c5 > 0) else 0
     if n15:
