@@ -68,7 +68,8 @@ const char* croft_status_string(croft_status s);
  *
  * Paper: the single reusable 1D plan covering all pencils ("option 4",
  * Sec. 5.1) and the three-axis schedule of Sec. 4.1.  Factorises each axis
- * into radix 16/8/4/2/3/5 stages, builds twiddle tables
+ * into radix 16/8/4/2/15/9/5/3 stages (the odd factors in the fewest
+ * stages of at most 16 points), builds twiddle tables
  * w = exp(-2 pi i r/n) in float64 with exact integer reduction of r and rounds
  * them to float32, and uploads them.
  *
