@@ -444,6 +444,31 @@ def measure_rows(croft, torch, dev, stream, flush, peak, only=None):  # noqa: PL
         err = max(float(torch.linalg.vector_norm((z - math.prod(d) * x).flatten()) /
                         torch.linalg.vector_norm((math.prod(d) * x).flatten())) for d, x, z in zip(dims, xs, zs))
         brow["roundtrip_rel_l2_max"] = err
+        # the autotuned plan (CROFT_BATCH_AUTO): times the four schedules on scratch buffers at
+        # creation (a fresh cache file, so it measures) and keeps the fastest
+        import tempfile
+        with tempfile.TemporaryDirectory() as td:
+            old_cache = os.environ.get("CROFT_TUNE_CACHE")
+            os.environ["CROFT_TUNE_CACHE"] = os.path.join(td, "tune.txt")
+            try:
+                t0 = time.perf_counter()
+                bp = croft.BatchPlan(dims)
+                t_tune = time.perf_counter() - t0
+                with bp:
+                    sh = stream.cuda_stream
+                    f_ms, b_ms, _ = time_transform(
+                        croft, torch, stream, flush, bp.handle,
+                        lambda: croft.croft_exec_batched_forward(bp.handle, xs, ys, sh),
+                        lambda: croft.croft_exec_batched_backward(bp.handle, ys, zs, sh))
+                    desc = bp.describe()
+            finally:
+                if old_cache is None:
+                    os.environ.pop("CROFT_TUNE_CACHE", None)
+                else:
+                    os.environ["CROFT_TUNE_CACHE"] = old_cache
+        t = f_ms + b_ms
+        brow["autotuned"] = {"ms_fwd": f_ms, "ms_bwd": b_ms, "gflops": fl / (t * 1e-3) / 1e9,
+                             "plan_creation_s": t_tune, "plan": desc}
         rows["batch96"] = brow
     return rows
 
