@@ -223,3 +223,38 @@ def test_slab_schedule_matches_oracle(croft_lib, dev, shape, slab_mb, monkeypatc
     assert oracle.rel_l2(yf.cpu().numpy(), oracle.forward(x)) <= tol(shape)
     assert oracle.rel_l2(yb.cpu().numpy(), oracle.backward(x)) <= tol(shape)
     assert oracle.rel_l2(zb.cpu().numpy(), x.size * x.astype(np.complex128)) <= tol(shape)
+
+
+def test_exec_captured_in_a_cuda_graph(croft_lib, dev):
+    """Forward, backward and a convolution captured into one CUDA graph (the passes' programmatic
+    dependent launches become graph edges) replay to the same bits as direct calls."""
+    shape = (64, 48, 40)
+    rng = np.random.default_rng(5)
+    x_np = (rng.standard_normal(shape) + 1j * rng.standard_normal(shape)).astype(np.complex64)
+    x = torch.from_numpy(x_np).cuda()
+    g = torch.rand(shape, dtype=torch.float32, device="cuda")
+    with croft_lib.Plan(*shape) as p:
+        y_ref = p.forward(x)
+        z_ref = p.backward(y_ref)
+        c_ref = p.convolve(x, g)
+        y = torch.empty_like(x)
+        z = torch.empty_like(x)
+        c = torch.empty_like(x)
+        s = torch.cuda.Stream()
+        s.wait_stream(torch.cuda.current_stream())
+        with torch.cuda.stream(s):
+            p.forward(x, y)  # warm-up outside the capture
+        torch.cuda.current_stream().wait_stream(s)
+        graph = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(graph, stream=s):
+            p.forward(x, y)
+            p.backward(y, z)
+            p.convolve(x, g, c)
+        y.zero_()
+        z.zero_()
+        c.zero_()
+        graph.replay()
+        torch.cuda.synchronize()
+    assert torch.equal(y.view(torch.int32), y_ref.view(torch.int32))
+    assert torch.equal(z.view(torch.int32), z_ref.view(torch.int32))
+    assert torch.equal(c.view(torch.int32), c_ref.view(torch.int32))
