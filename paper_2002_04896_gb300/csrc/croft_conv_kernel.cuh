@@ -66,6 +66,62 @@ struct ConvShape {
     static constexpr int MIN_BLOCKS = TIGHT ? 4 : ((sizeof(C) == 8 && T == 32) ? 2 : 0);
 };
 
+// The last forward stage, the multiply by G and the first backward stage, in registers.
+// Valid when the schedule's first and last radices are equal (R): the last stage's
+// butterfly b (b < N/R, so k = b) produces outputs b + j*N/R, which are exactly the
+// inputs of butterfly b of the first stage of the next transform.  Reads the last
+// forward stage's input from `src`, multiplies its outputs by G (from the G tile) and
+// conjugates them, applies the first stage of the backward transform (no twiddles)
+// and stores its outputs (index b*R + j) to `dst`.  `mid` separates all reads from
+// the stores (and publishes the G copies).
+template <int N, int T, int W, class Src, class Mid, class Dst, class R>
+__device__ __forceinline__ void conv_middle(const Src& src, const Mid& mid, const Dst& dst, const R* gcol,
+                                            const typename Src::value_type* stw, int lane, bool ok) {
+    using C = typename Src::value_type;
+    constexpr CroftSched sc = croft_make_sched(N);
+    constexpr int S = sc.count - 1;
+    constexpr int RAD = sc.r[S];
+    constexpr int P = croft_sched_p(sc, S);
+    constexpr int NB = N / RAD;
+    static_assert(sc.r[0] == RAD && P == NB, "first and last radix must agree");
+    constexpr int QM = (NB + T - 1) / T;
+    C v[QM][RAD];
+#pragma unroll
+    for (int q = 0; q < QM; ++q) {
+        const int b = lane + q * T;
+        if (ok && (NB % T == 0 || b < NB)) {
+#pragma unroll
+            for (int j = 0; j < RAD; ++j) v[q][j] = src.load(b + j * NB);
+        }
+    }
+    mid();
+#pragma unroll
+    for (int q = 0; q < QM; ++q) {
+        const int b = lane + q * T;
+        if (ok && (NB % T == 0 || b < NB)) {
+            if (P > 1) {
+                const C* w = stw + (P - 1) + b;
+#pragma unroll
+                for (int j = 1; j < RAD; ++j) v[q][j] = cmul(v[q][j], w[(j - 1) * P]);
+            }
+            dft<RAD>(v[q]);
+#pragma unroll
+            for (int j = 0; j < RAD; ++j) {
+                const R ga = gcol[(b + j * P) * W];
+                v[q][j] = mkc<C>(v[q][j].x * ga, -(v[q][j].y * ga));
+            }
+            dft<RAD>(v[q]);
+#pragma unroll
+            for (int j = 0; j < RAD; ++j) dst.store(b * RAD + j, v[q][j]);
+        }
+    }
+}
+
+template <int N>
+constexpr bool conv_fuses_middle() {
+    return croft_make_sched(N).count >= 1 && croft_make_sched(N).r[0] == croft_make_sched(N).r[croft_make_sched(N).count - 1];
+}
+
 // Shared memory: [twiddles: tw_pad][tile: N x W complex][G tile: N x W real].
 template <int N, class C>
 __device__ __forceinline__ void conv_body(const C* in, C* out, const typename CxScalar<C>::T* g, const PassArgs& A) {
@@ -102,6 +158,24 @@ __device__ __forceinline__ void conv_body(const C* in, C* out, const typename Cx
     const ScaleConjCol<C, W> scaled{tile + c, gtile + c};
     const GlobalOutT<C> dst{out + base, A.M, -1.f};
 
+    if constexpr (conv_fuses_middle<N>()) {
+        // forward stages but the last; the last, G and the first backward stage in registers
+        // (conv_middle); the remaining backward stages
+        if constexpr (sc.count == 1) {
+            asm volatile("cp.async.wait_all;" ::: "memory");
+            conv_middle<N, T, W>(src, CtaBarrier{}, dst, gtile + c, stw, lane, ok);
+        } else {
+            fft_stage<N, 0, T>(src, NoBarrier{}, work, stw, lane, ok);
+            __syncthreads();
+            smem_stages<N, 1, sc.count - 1, T>(work, stw, lane, ok);
+            asm volatile("cp.async.wait_all;" ::: "memory");
+            conv_middle<N, T, W>(work, CtaBarrier{}, work, gtile + c, stw, lane, ok);
+            __syncthreads();
+            smem_stages<N, 1, sc.count - 1, T>(work, stw, lane, ok);
+            fft_stage<N, sc.count - 1, T>(work, NoBarrier{}, dst, stw, lane, ok);
+        }
+        return;
+    }
     // forward transform of the column; its last stage leaves conj(G * Y) in the tile.
     // (The barrier inside the last stage also publishes every thread's G copies.)
     if constexpr (sc.count == 1) {
