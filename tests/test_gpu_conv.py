@@ -197,3 +197,29 @@ def test_argument_errors(croft_lib, dev):
     finally:
         c.croft_plan_destroy(bp)
     torch.cuda.synchronize()
+
+
+@pytest.mark.parametrize("name", ["pme480", "pme512"])
+def test_full_size_properties(croft_lib, dev, name):
+    """At the bench's full sizes (the oracle is too slow for the whole grid): the fused convolution
+    equals forward, an elementwise multiply and backward run as separate calls, and with the real
+    charge grid and the real even influence function the result is real with zero sum."""
+    x_np = S.config_input(name)
+    g_np = S.pme_influence(x_np.shape)
+    x = torch.from_numpy(x_np).cuda()
+    g = torch.from_numpy(g_np).cuda()
+    with croft_lib.Plan(*x_np.shape) as p:
+        c = p.convolve(x, g)
+        y = p.forward(x)
+        y.mul_(g)
+        s = p.backward(y, y)
+        torch.cuda.synchronize()
+    n = x_np.size
+    diff = float(torch.linalg.vector_norm((c - s).flatten()) / torch.linalg.vector_norm(s.flatten()))
+    assert diff <= tol(x_np.shape), diff
+    scale = float(c.real.abs().max())
+    assert float(c.imag.abs().max()) <= 1e-4 * scale
+    assert abs(complex(c.to(torch.complex128).sum())) <= 1e-4 * float(c.abs().to(torch.float64).sum())
+    del x, g, c, y, s
+    torch.cuda.empty_cache()
+    assert n > 0
