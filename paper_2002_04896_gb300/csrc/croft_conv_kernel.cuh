@@ -20,6 +20,8 @@
 // the last forward stage stores conj(G * Y) into the tile, the forward stages
 // run again on it, and the final store conjugates.
 #pragma once
+#include <type_traits>
+
 #include "croft_fft_core.cuh"
 #include "croft_internal.h"
 
@@ -74,11 +76,12 @@ struct ConvShape {
 // conjugates them, applies the first stage of the backward transform (no twiddles)
 // and stores its outputs (index b*R + j) to `dst`.  `mid` separates all reads from
 // the stores (and publishes the G copies).
-template <int N, int T, int W, class Src, class Mid, class Dst, class R>
+template <class SchedT, int T, int W, class Src, class Mid, class Dst, class R>
 __device__ __forceinline__ void conv_middle(const Src& src, const Mid& mid, const Dst& dst, const R* gcol,
                                             const typename Src::value_type* stw, int lane, bool ok) {
     using C = typename Src::value_type;
-    constexpr CroftSched sc = croft_make_sched(N);
+    constexpr int N = SchedT::N;
+    constexpr CroftSched sc = SchedT::get();
     constexpr int S = sc.count - 1;
     constexpr int RAD = sc.r[S];
     constexpr int P = croft_sched_p(sc, S);
@@ -117,9 +120,18 @@ __device__ __forceinline__ void conv_middle(const Src& src, const Mid& mid, cons
     }
 }
 
-template <int N>
+// The schedule of the fused pass: the column passes' (croft_pass_sched).
+template <int N, class C>
+struct ConvSched {
+    static constexpr int N_ = N;
+    static constexpr bool even = croft_even_pow2_pass(N, LAYOUT_COL, (int)sizeof(C));
+};
+template <int N, class C>
+using ConvSchedT = typename std::conditional<ConvSched<N, C>::even, EvenPow2Sched<N>, DefaultSched<N>>::type;
+
+template <class SchedT>
 constexpr bool conv_fuses_middle() {
-    return croft_make_sched(N).count >= 1 && croft_make_sched(N).r[0] == croft_make_sched(N).r[croft_make_sched(N).count - 1];
+    return SchedT::get().count >= 1 && SchedT::get().r[0] == SchedT::get().r[SchedT::get().count - 1];
 }
 
 // Shared memory: [twiddles: tw_pad][tile: N x W complex][G tile: N x W real].
@@ -128,7 +140,8 @@ __device__ __forceinline__ void conv_body(const C* in, C* out, const typename Cx
     using R = typename CxScalar<C>::T;
     constexpr int T = ConvShape<N, C>::T;
     constexpr int W = ConvShape<N, C>::W;
-    constexpr CroftSched sc = croft_make_sched(N);
+    using CS = ConvSchedT<N, C>;
+    constexpr CroftSched sc = CS::get();
     extern __shared__ __align__(16) unsigned char smem_raw[];
     C* stw = reinterpret_cast<C*>(smem_raw);
     C* tile = stw + A.tw_pad;
@@ -158,21 +171,21 @@ __device__ __forceinline__ void conv_body(const C* in, C* out, const typename Cx
     const ScaleConjCol<C, W> scaled{tile + c, gtile + c};
     const GlobalOutT<C> dst{out + base, A.M, -1.f};
 
-    if constexpr (conv_fuses_middle<N>()) {
+    if constexpr (conv_fuses_middle<CS>()) {
         // forward stages but the last; the last, G and the first backward stage in registers
         // (conv_middle); the remaining backward stages
         if constexpr (sc.count == 1) {
             asm volatile("cp.async.wait_all;" ::: "memory");
-            conv_middle<N, T, W>(src, CtaBarrier{}, dst, gtile + c, stw, lane, ok);
+            conv_middle<CS, T, W>(src, CtaBarrier{}, dst, gtile + c, stw, lane, ok);
         } else {
-            fft_stage<N, 0, T>(src, NoBarrier{}, work, stw, lane, ok);
+            fft_stage_s<CS, 0, T>(src, NoBarrier{}, work, stw, lane, ok);
             __syncthreads();
-            smem_stages<N, 1, sc.count - 1, T>(work, stw, lane, ok);
+            smem_stages_s<CS, 1, sc.count - 1, T>(work, stw, lane, ok);
             asm volatile("cp.async.wait_all;" ::: "memory");
-            conv_middle<N, T, W>(work, CtaBarrier{}, work, gtile + c, stw, lane, ok);
+            conv_middle<CS, T, W>(work, CtaBarrier{}, work, gtile + c, stw, lane, ok);
             __syncthreads();
-            smem_stages<N, 1, sc.count - 1, T>(work, stw, lane, ok);
-            fft_stage<N, sc.count - 1, T>(work, NoBarrier{}, dst, stw, lane, ok);
+            smem_stages_s<CS, 1, sc.count - 1, T>(work, stw, lane, ok);
+            fft_stage_s<CS, sc.count - 1, T>(work, NoBarrier{}, dst, stw, lane, ok);
         }
         return;
     }
@@ -180,23 +193,23 @@ __device__ __forceinline__ void conv_body(const C* in, C* out, const typename Cx
     // (The barrier inside the last stage also publishes every thread's G copies.)
     if constexpr (sc.count == 1) {
         asm volatile("cp.async.wait_all;" ::: "memory");
-        fft_stage<N, 0, T>(src, CtaBarrier{}, scaled, stw, lane, ok);
+        fft_stage_s<CS, 0, T>(src, CtaBarrier{}, scaled, stw, lane, ok);
     } else {
-        fft_stage<N, 0, T>(src, NoBarrier{}, work, stw, lane, ok);
+        fft_stage_s<CS, 0, T>(src, NoBarrier{}, work, stw, lane, ok);
         __syncthreads();
-        smem_stages<N, 1, sc.count - 1, T>(work, stw, lane, ok);
+        smem_stages_s<CS, 1, sc.count - 1, T>(work, stw, lane, ok);
         asm volatile("cp.async.wait_all;" ::: "memory");
-        fft_stage<N, sc.count - 1, T>(work, CtaBarrier{}, scaled, stw, lane, ok);
+        fft_stage_s<CS, sc.count - 1, T>(work, CtaBarrier{}, scaled, stw, lane, ok);
     }
     __syncthreads();
     // backward transform along the same axis: forward stages on the conjugated tile, conjugated store
     if constexpr (sc.count == 1) {
-        fft_stage<N, 0, T>(work, NoBarrier{}, dst, stw, lane, ok);
+        fft_stage_s<CS, 0, T>(work, NoBarrier{}, dst, stw, lane, ok);
     } else {
-        fft_stage<N, 0, T>(work, CtaBarrier{}, work, stw, lane, ok);
+        fft_stage_s<CS, 0, T>(work, CtaBarrier{}, work, stw, lane, ok);
         __syncthreads();
-        smem_stages<N, 1, sc.count - 1, T>(work, stw, lane, ok);
-        fft_stage<N, sc.count - 1, T>(work, NoBarrier{}, dst, stw, lane, ok);
+        smem_stages_s<CS, 1, sc.count - 1, T>(work, stw, lane, ok);
+        fft_stage_s<CS, sc.count - 1, T>(work, NoBarrier{}, dst, stw, lane, ok);
     }
 }
 

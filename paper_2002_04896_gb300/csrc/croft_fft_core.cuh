@@ -158,6 +158,11 @@ struct DefaultSched {
     __host__ __device__ static constexpr CroftSched get() { return croft_make_sched(N_); }
 };
 template <int N_>
+struct EvenPow2Sched {  // the near-equal power-of-two split (croft_pass_sched)
+    static constexpr int N = N_;
+    __host__ __device__ static constexpr CroftSched get() { return croft_make_sched(N_, true); }
+};
+template <int N_>
 struct Tc16Sched {
     static constexpr int N = N_;
     __host__ __device__ static constexpr CroftSched get() { return croft_make_sched_tc(N_); }
@@ -236,6 +241,29 @@ __device__ __forceinline__ void fft_pencil(const Src& src, const Sm& work, const
         __syncthreads();
         smem_stages<N, 1, sc.count - 1, T>(work, stw, lane, ok);
         fft_stage<N, sc.count - 1, T>(work, NoBarrier{}, dst, stw, lane, ok);
+    }
+}
+
+// smem_stages / fft_pencil for an explicit schedule type (SchedT::N, SchedT::get()).
+template <class SchedT, int S, int E, int T, class Sm>
+__device__ __forceinline__ void smem_stages_s(const Sm& sm, const typename Sm::value_type* stw, int lane, bool ok) {
+    if constexpr (S < E) {
+        fft_stage_s<SchedT, S, T>(sm, CtaBarrier{}, sm, stw, lane, ok);
+        __syncthreads();
+        smem_stages_s<SchedT, S + 1, E, T>(sm, stw, lane, ok);
+    }
+}
+template <class SchedT, int T, class Src, class Sm, class Dst>
+__device__ __forceinline__ void fft_pencil_s(const Src& src, const Sm& work, const Dst& dst,
+                                             const typename Src::value_type* stw, int lane, bool ok) {
+    constexpr CroftSched sc = SchedT::get();
+    if constexpr (sc.count == 1) {
+        fft_stage_s<SchedT, 0, T>(src, NoBarrier{}, dst, stw, lane, ok);
+    } else {
+        fft_stage_s<SchedT, 0, T>(src, NoBarrier{}, work, stw, lane, ok);
+        __syncthreads();
+        smem_stages_s<SchedT, 1, sc.count - 1, T>(work, stw, lane, ok);
+        fft_stage_s<SchedT, sc.count - 1, T>(work, NoBarrier{}, dst, stw, lane, ok);
     }
 }
 

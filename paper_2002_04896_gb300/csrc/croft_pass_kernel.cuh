@@ -61,8 +61,13 @@ __device__ __forceinline__ void pass_body(const C* in, C* out, const PassArgs& A
         const long long b = col / A.M;
         const long long m = col - b * A.M;
         const long long base = b * (long long)N * A.M + m;
-        fft_pencil<N, T>(GlobalInT<C>{in + base, A.M, A.isign}, SmemColFixed<C, (WC > 0 ? WC : 1)>{sbuf + c},
-                         GlobalOutT<C>{out + base, A.M, A.isign}, stw, lane, ok);
+        const GlobalInT<C> src{in + base, A.M, A.isign};
+        const SmemColFixed<C, (WC > 0 ? WC : 1)> work{sbuf + c};
+        const GlobalOutT<C> dst{out + base, A.M, A.isign};
+        if constexpr (croft_even_pow2_pass(N, LAYOUT_COL, (int)sizeof(C)))
+            fft_pencil_s<EvenPow2Sched<N>, T>(src, work, dst, stw, lane, ok);
+        else
+            fft_pencil<N, T>(src, work, dst, stw, lane, ok);
     }
 }
 

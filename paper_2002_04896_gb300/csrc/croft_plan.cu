@@ -232,7 +232,8 @@ static croft_status add_axis_pass(croft_plan p, int axis, int x0 = 0, int nxs = 
     const char* pe = getenv("CROFT_PIPE");
     const bool allow_pipe = pe && pe[0] == '1';
     const bool f64 = p->dtype == CROFT_C2C_F64;
-    if (allow_pipe && !f64 && !p->axis_tc[axis] && pipe_kernel_for(layout, n) && (layout == LAYOUT_ROW || (M % 2) == 0)) {
+    if (allow_pipe && !f64 && !p->axis_tc[axis] && pipe_kernel_for(layout, n) && (layout == LAYOUT_ROW || (M % 2) == 0) &&
+        !croft_even_pow2_pass(n, layout, 8)) {  // (the pipelined kernel runs the default schedule)
         PassLaunch L;
         if (shape_pipe(L, layout, n, M, N / n)) {
             L.pa.tw = p->tw_dev[axis];
@@ -326,6 +327,11 @@ static void plan_conv(croft_plan p) {
     const long long N = (long long)p->dims[0] * p->dims[1] * p->dims[2];
     const long long M = (axis == 2) ? 1 : (axis == 1 ? (long long)p->dims[2] : (long long)p->dims[1] * p->dims[2]);
     if (f64 ? !conv64_kernel_for(n) : !conv_kernel_for(n)) return;
+    // the fused kernel runs the column schedule; the axis's twiddle table follows its pass's
+    const CroftSched sa = croft_pass_sched(n, Lp.layout, f64 ? 16 : 8), sb = croft_pass_sched(n, LAYOUT_COL, f64 ? 16 : 8);
+    if (sa.count != sb.count) return;
+    for (int i = 0; i < sa.count; ++i)
+        if (sa.r[i] != sb.r[i]) return;
     PassLaunch L;
     // the kernel's column width is a compile-time constant (croft_conv_width)
     const int want_w = croft_conv_width(n, f64 ? 16 : 8);
@@ -422,7 +428,11 @@ static croft_status create_impl(croft_plan* out, int nx, int ny, int nz, croft_d
             ns = sc.count;
             for (int i = 0; i < ns; ++i) rad[i] = sc.r[i];
         } else {
-            ns = factorize(n, rad, CROFT_MAX_STAGES);
+            // the schedule of the axis's pass (a unit element stride makes it a row pass)
+            const long long M = (axis == 2) ? 1 : (axis == 1 ? (long long)nz : (long long)ny * nz);
+            const CroftSched sc = croft_pass_sched(n, M == 1 ? LAYOUT_ROW : LAYOUT_COL, dtype == CROFT_C2C_F64 ? 16 : 8);
+            ns = sc.count;
+            for (int i = 0; i < ns; ++i) rad[i] = sc.r[i];
         }
         if (ns < 1) return fail(p, CROFT_ERR_UNSUPPORTED_SIZE);
         if (dtype == CROFT_C2C_F64) {
@@ -525,7 +535,7 @@ int croft_plan_describe(croft_plan plan, char* buf, int cap) {
         snprintf(tmp, sizeof(tmp), " | %s:%s%s%s n=%d radix=", an[plan->pass_axis[i]], L.layout == LAYOUT_ROW ? "row" : "col",
                  L.tc ? "+tc" : "", L.pipe ? "+tma" : "", L.args.n);
         s += tmp;
-        CroftSched sc = L.tc ? croft_make_sched_tc(L.args.n) : croft_make_sched(L.args.n);
+        CroftSched sc = L.tc ? croft_make_sched_tc(L.args.n) : croft_pass_sched(L.args.n, L.layout, L.f64 ? 16 : 8);
         for (int st = 0; st < sc.count; ++st) {
             snprintf(tmp, sizeof(tmp), "%s%d", st ? "x" : "", sc.r[st]);
             s += tmp;

@@ -27,6 +27,8 @@
 // copy of the cluster has landed, so no CTA exits while its shared memory is
 // still read or written by a copy.  The mbarrier wait is bounded.
 #pragma once
+#include <type_traits>
+
 #include "croft_fft_core.cuh"
 #include "croft_internal.h"
 
@@ -81,7 +83,9 @@ __global__ void __launch_bounds__(PlaneShape<NY, NZ, C>::THREADS) croft_plane_ke
     const float2* in, float2* out, const __grid_constant__ PlaneArgs A) {
     using Sh = PlaneShape<NY, NZ, C>;
     constexpr CroftSched scz = croft_make_sched(NZ);
-    constexpr CroftSched scy = croft_make_sched(NY);
+    // the y phase runs the y axis's column-pass schedule (its twiddle table follows it)
+    using YS = typename std::conditional<croft_even_pow2_pass(NY, LAYOUT_COL, 8), EvenPow2Sched<NY>, DefaultSched<NY>>::type;
+    constexpr CroftSched scy = YS::get();
     extern __shared__ __align__(16) float2 smem[];
     __shared__ __align__(8) uint64_t ybar;
     float2* twz = smem;
@@ -172,12 +176,12 @@ __global__ void __launch_bounds__(PlaneShape<NY, NZ, C>::THREADS) croft_plane_ke
         const SmemCol col{ytile + c, Sh::CZ};
         const GlobalOut dst{out + off + z, NZ, A.isign};
         if constexpr (scy.count == 1) {
-            fft_stage<NY, 0, Sh::TY>(col, NoBarrier{}, dst, twy, lane, ok);
+            fft_stage_s<YS, 0, Sh::TY>(col, NoBarrier{}, dst, twy, lane, ok);
         } else {
-            fft_stage<NY, 0, Sh::TY>(col, CtaBarrier{}, col, twy, lane, ok);
+            fft_stage_s<YS, 0, Sh::TY>(col, CtaBarrier{}, col, twy, lane, ok);
             __syncthreads();
-            smem_stages<NY, 1, scy.count - 1, Sh::TY>(col, twy, lane, ok);
-            fft_stage<NY, scy.count - 1, Sh::TY>(col, NoBarrier{}, dst, twy, lane, ok);
+            smem_stages_s<YS, 1, scy.count - 1, Sh::TY>(col, twy, lane, ok);
+            fft_stage_s<YS, scy.count - 1, Sh::TY>(col, NoBarrier{}, dst, twy, lane, ok);
         }
     }
     if constexpr (C > 1) asm volatile("barrier.cluster.wait.aligned;" ::: "memory");  // (2): no copy in flight

@@ -26,7 +26,10 @@ struct CroftSched {
 // 5 as radix 15, then the remaining 5s and 3 (each stage is a shared-memory round
 // trip and a barrier).  The first stage needs no twiddles, so the largest radix
 // goes there.
-CROFT_HD constexpr CroftSched croft_make_sched(int n) {
+//
+// even_pow2: the power-of-two part in ceil(a/4) stages of near-equal size instead
+// (croft_pass_sched picks it for the column passes of 32-thread pencils).
+CROFT_HD constexpr CroftSched croft_make_sched(int n, bool even_pow2 = false) {
     CroftSched s{0, {0, 0, 0, 0, 0, 0, 0, 0}};
     if (n < 1 || n > CROFT_MAX_N) {
         s.count = -1;
@@ -41,7 +44,13 @@ CROFT_HD constexpr CroftSched croft_make_sched(int n) {
         return s;
     }
     int k = 0;
-    for (int aa = a; aa > 0; aa -= 4) s.r[k++] = 1 << (aa >= 4 ? 4 : aa);
+    if (even_pow2 && a > 0) {
+        const int st = (a + 3) / 4;
+        const int base = a / st, extra = a % st;
+        for (int i = 0; i < st; ++i) s.r[k++] = 1 << (base + (i < extra ? 1 : 0));
+    } else {
+        for (int aa = a; aa > 0; aa -= 4) s.r[k++] = 1 << (aa >= 4 ? 4 : aa);
+    }
     const int n9 = c3 / 2;
     int r3 = c3 % 2;
     const int n15 = (r3 && c5 > 0) ? 1 : 0;
@@ -131,6 +140,19 @@ CROFT_HD constexpr int croft_threads_per_pencil(int n) {
     int p = 1;
     while (p < t) p *= 2;
     return p;
+}
+
+// The schedule of a pass over a length-n axis (layout 0 = ROW, 1 = COL; es = complex
+// element size): the column passes of complex64 32-thread pencils (lengths 270..512,
+// bounded to 40 registers) take the near-equal power-of-two split - at 480 the
+// column passes ran 330 / 349 us with 15·8·4 against 340 / 362 with 16·15·2, while the
+// row pass prefers 16·15·2 (285 vs 294 us) - every other pass the radix-16 one.
+// Twiddle tables are built for the pass's schedule.
+CROFT_HD constexpr bool croft_even_pow2_pass(int n, int layout, int es) {
+    return layout == 1 && es == 8 && croft_threads_per_pencil(n) == 32;
+}
+CROFT_HD constexpr CroftSched croft_pass_sched(int n, int layout, int es) {
+    return croft_make_sched(n, croft_even_pow2_pass(n, layout, es));
 }
 
 // Column-tile width (columns per CTA) of a COL pass - a compile-time constant of
