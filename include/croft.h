@@ -140,7 +140,7 @@ croft_status croft_plan_create_schedule(croft_plan* out, int nx, int ny, int nz,
  *               and keep the fastest; the choice is cached in the text file named
  *               by $CROFT_TUNE_CACHE (default $HOME/.croft_tune_cache.txt), keyed by
  *               the sizes, GPU name and CUDA runtime version.  CROFT_TUNE=off skips
- *               the timing and uses ONE_LAUNCH.
+ *               the timing and uses GROUPED (the fastest in every measurement so far).
  *   Grids with an axis > 128 always run on their own single-grid plan.
  * croft_plan_create_batched: the same with CROFT_BATCH_AUTO.
  * Paper: many 1D FFTs under one plan ("option 4") and the chunk count K

@@ -430,7 +430,7 @@ static croft_status autotune(croft_plan plan) {
     char* buf = nullptr;
     if (dev_alloc((void**)&buf, total) != cudaSuccess) {
         cudaGetLastError();
-        return configure(b, CROFT_BATCH_ONE_LAUNCH);
+        return configure(b, CROFT_BATCH_GROUPED);
     }
     cudaMemset(buf, 0, total);
     std::vector<void*> ptrs(b->count);
@@ -525,7 +525,7 @@ croft_status croft_plan_create_batched_mode(croft_plan* out, int count, const in
     croft_status st;
     const char* tune = getenv("CROFT_TUNE");
     if (mode == CROFT_BATCH_AUTO && !(tune && strcmp(tune, "off") == 0)) st = autotune(p);
-    else st = configure(p->batch, mode == CROFT_BATCH_AUTO ? CROFT_BATCH_ONE_LAUNCH : mode);
+    else st = configure(p->batch, mode == CROFT_BATCH_AUTO ? CROFT_BATCH_GROUPED : mode);  // (the usual winner)
     if (st == CROFT_OK) st = build_graphs(p->batch);
     if (st != CROFT_OK) {
         cudaGetLastError();

@@ -49,6 +49,12 @@ def test_batched_plan_oom_at_every_allocation(croft_lib):
     assert n >= 5
 
 
+def test_grouped_batched_plan_oom_at_every_allocation(croft_lib):
+    dims = [(48, 60, 64), (8, 6, 4), (4, 144, 10)]
+    n = _sweep(croft_lib, lambda: croft_lib.croft_plan_create_batched_status(dims, 0, croft_lib.CROFT_BATCH_GROUPED))
+    assert n >= 4  # pinned segment table, segments, CTA map, twiddle pool (+ the single-grid plan of the 144 grid)
+
+
 def test_destroy_releases_everything(croft_lib):
     base = croft_lib.croft_debug_live_allocations()
     with croft_lib.Plan(32, 32, 32):
