@@ -19,12 +19,20 @@ static pass_fn col_kernel(int w) {
     constexpr int W = croft_col_width(N, 8);
     if (w != W) return nullptr;
     if constexpr (croft_col_minb(N, 8) > 1) return croft_pass_kernel_bounded<LAYOUT_COL, N, float2, W, croft_col_minb(N, 8)>;
+    else if constexpr (croft_pass_minb(N, 8) > 0)
+        return croft_pass_kernel_bounded<LAYOUT_COL, N, float2, W, croft_pass_minb(N, 8), 256>;
     else return croft_pass_kernel<LAYOUT_COL, N, float2, W>;
+}
+
+template <int N>
+static pass_fn row_kernel() {
+    if constexpr (croft_pass_minb(N, 8) > 0) return croft_pass_kernel_bounded<LAYOUT_ROW, N, float2, 0, croft_pass_minb(N, 8), 256>;
+    else return croft_pass_kernel<LAYOUT_ROW, N>;
 }
 
 pass_fn CROFT_CAT(lookup_pass_kernel_group_, CROFT_GROUP)(int layout, int n, int w) {
 #define CROFT_CASE(N) \
-    case N: return layout == LAYOUT_ROW ? croft_pass_kernel<LAYOUT_ROW, N> : col_kernel<N>(w);
+    case N: return layout == LAYOUT_ROW ? row_kernel<N>() : col_kernel<N>(w);
     switch (n) {
         CROFT_CAT(CROFT_SIZES_, CROFT_GROUP)(CROFT_CASE)
         default: return nullptr;

@@ -79,10 +79,11 @@ __global__ void __launch_bounds__(512) croft_pass_kernel(const C* in, C* out, co
     pass_body<LAYOUT, N, C, WC>(in, out, A);
 }
 
-// The same with registers bounded for MINB CTAs of 512 threads per SM (croft_col_minb).
-template <int LAYOUT, int N, class C, int WC, int MINB>
-__global__ void __launch_bounds__(512, MINB) croft_pass_kernel_bounded(const C* in, C* out,
-                                                                        const __grid_constant__ PassArgs A) {
+// The same with registers bounded for MINB CTAs of MAXT threads per SM (croft_col_minb,
+// croft_pass_minb).
+template <int LAYOUT, int N, class C, int WC, int MINB, int MAXT = 512>
+__global__ void __launch_bounds__(MAXT, MINB) croft_pass_kernel_bounded(const C* in, C* out,
+                                                                         const __grid_constant__ PassArgs A) {
     pass_body<LAYOUT, N, C, WC>(in, out, A);
 }
 

@@ -178,6 +178,12 @@ CROFT_HD constexpr int croft_col_width(int n, int es) {
 // of 320^3 .. 512^3 grids.
 CROFT_HD constexpr int croft_col_minb(int n, int es) { return (es == 8 && croft_threads_per_pencil(n) == 32) ? 3 : 1; }
 
+// CTAs per SM that a 256-thread pass kernel's registers must allow (0: no bound).  The
+// 256-point passes (16 threads per pencil, 16 pencils or columns per CTA) take ~50-52
+// registers unbounded - four CTAs per SM by registers; bounded to five (48 registers,
+// no spills) they keep more loads in flight.
+CROFT_HD constexpr int croft_pass_minb(int n, int es) { return (es == 8 && n == 256) ? 5 : 0; }
+
 // Column-tile width of the fused convolution pass: the same as a COL pass (8 columns
 // measured slower at every size from 384 to 512: 480^3 774 vs 690 us).
 CROFT_HD constexpr int croft_conv_width(int n, int es) { return croft_col_width(n, es); }
