@@ -12,11 +12,15 @@
 
 namespace croft {
 
-// One COL kernel per length: tile width croft_col_width, launch bound croft_col_minb.
-// w: the width asked for (a kernel exists only for that one).
+// One COL kernel per length: tile width croft_col_width, launch bound croft_col_minb;
+// lengths of 32-thread pencils add the narrow short-stride kernel (croft_col_width_at).
+// w: the width asked for (nullptr when no kernel is built for it).
 template <int N>
 static pass_fn col_kernel(int w) {
     constexpr int W = croft_col_width(N, 8);
+    if constexpr (croft_threads_per_pencil(N) == 32 && W != kColNarrowWidth)
+        if (w == kColNarrowWidth)
+            return croft_pass_kernel_bounded<LAYOUT_COL, N, float2, kColNarrowWidth, kColNarrowMinb, kColNarrowWidth * 32>;
     if (w != W) return nullptr;
     if constexpr (croft_col_minb(N, 8) > 1) return croft_pass_kernel_bounded<LAYOUT_COL, N, float2, W, croft_col_minb(N, 8)>;
     else if constexpr (croft_pass_minb(N, 8) > 0)

@@ -45,7 +45,7 @@ bool shape_pass(PassLaunch& L, int layout, int n, long long M, long long ncols, 
         if (tc) {
             while (W * 2 * T <= 256) W *= 2;
         } else {
-            W = croft_col_width(n, (int)es);  // the width the kernels are built for
+            W = croft_col_width_at(n, (int)es, M * es);  // a width the kernels are built for
         }
         if (want_w >= 1 && !tc) W = want_w;
         while (W > 1 && (W * T > max_threads || (A.tw_pad + (long long)n * W) * es > smem_cap)) W /= 2;

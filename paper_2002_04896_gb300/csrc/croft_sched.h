@@ -178,6 +178,22 @@ CROFT_HD constexpr int croft_col_width(int n, int es) {
 // of 320^3 .. 512^3 grids.
 CROFT_HD constexpr int croft_col_minb(int n, int es) { return (es == 8 && croft_threads_per_pencil(n) == 32) ? 3 : 1; }
 
+// Short-stride column passes of complex64 32-thread pencils (the y pass: the axis's
+// elements at most 16 KB apart) take 8-column, 256-thread tiles bounded to five CTAs
+// per SM instead (48 registers, 0-52 bytes of spills): 512^3 y pass 455 -> 414 us,
+// 320^3 121 -> 115 us, 360-point y pass of 384x360x320 162 -> 160 us, 480^3 330 ->
+// 332 us.  Across the x pass's megabyte strides the 64-byte row pieces lose (512^3
+// 487 -> 649 us), so that pass keeps croft_col_width's 16 columns.
+constexpr int kColNarrowWidth = 8;
+constexpr int kColNarrowMinb = 5;
+CROFT_HD constexpr bool croft_col_narrow(int n, int es, long long stride_bytes) {
+    return es == 8 && croft_threads_per_pencil(n) == 32 && stride_bytes <= 16 * 1024;
+}
+// Column-tile width of a COL pass over a length-n axis whose elements lie stride_bytes apart.
+CROFT_HD constexpr int croft_col_width_at(int n, int es, long long stride_bytes) {
+    return croft_col_narrow(n, es, stride_bytes) ? kColNarrowWidth : croft_col_width(n, es);
+}
+
 // CTAs per SM that a 256-thread pass kernel's registers must allow (0: no bound).  The
 // 256-point passes (16 threads per pencil, 16 pencils or columns per CTA) take ~50-52
 // registers unbounded - four CTAs per SM by registers; bounded to five (48 registers,

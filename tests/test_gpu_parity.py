@@ -62,6 +62,37 @@ def test_every_axis_length_on_every_axis(croft_lib, dev, n):
         assert e <= tol(shape), (shape, e)
 
 
+LONG_PENCIL_SIZES = [n for n in _supported_sizes(512) if n > 256]  # 32 threads per pencil
+
+
+def _pass_desc(desc, axis):
+    part = desc[desc.index(axis + ":"):]
+    return part.split(" | ")[0]
+
+
+@pytest.mark.parametrize("n", LONG_PENCIL_SIZES)
+def test_long_pencil_x_pass_over_wide_stride(croft_lib, dev, n):
+    """A length of 32-thread pencils as the x axis with its elements 18 KB apart takes the
+    16-column tile (the y pass of the length-n axis above, 40 bytes apart, the 8-column one);
+    2250 columns leave a ragged last tile."""
+    rng = np.random.default_rng(1000 + n)
+    shape = (n, 45, 50)
+    x = (rng.uniform(-1, 1, shape) + 1j * rng.uniform(-1, 1, shape)).astype(np.complex64)
+    with croft_lib.Plan(*shape) as p:
+        assert " W=16 " in _pass_desc(p.describe(), "x"), p.describe()
+    y = run(croft_lib, x)
+    e = oracle.rel_l2(y, oracle.forward(x))
+    assert e <= tol(shape), (shape, e)
+
+
+def test_column_width_follows_the_stride(croft_lib, dev):
+    """512^3: the y pass (4 KB stride) runs 8-column tiles, the x pass (2 MB stride) 16."""
+    with croft_lib.Plan(512, 512, 512) as p:
+        d = p.describe()
+    assert " W=8 block=256 " in _pass_desc(d, "y"), d
+    assert " W=16 block=512 " in _pass_desc(d, "x"), d
+
+
 @pytest.mark.parametrize("shape", [(1, 1, 1), (1, 1, 8), (1, 16, 1), (32, 1, 1), (2, 2, 2), (6, 10, 15),
                                    (64, 48, 40), (5, 3, 1), (1, 60, 128)])
 def test_small_and_degenerate_shapes(croft_lib, dev, shape):
