@@ -180,7 +180,11 @@ void group_state_fill(GroupState* s, void* const* in, void* const* out) {
 }
 
 // Adds [segment upload] -> pass 0 launches -> pass 1 launches -> pass 2 launches to g.
-croft_status group_graph_add(GroupState* s, cudaGraph_t g, float isign) {
+// With pdl, the edges from one pass's launches to the next pass's are programmatic:
+// the next pass's CTAs may become resident (and load their twiddles) while the
+// previous pass drains, and wait in the kernel (griddepcontrol.wait) for every
+// upstream launch to complete before they read the grid.
+croft_status group_graph_add(GroupState* s, cudaGraph_t g, float isign, bool pdl) {
     if (s->nseg == 0) return CROFT_OK;
     cudaGraphNode_t up;
     if (cudaGraphAddMemcpyNode1D(&up, g, nullptr, 0, s->d_segs, s->staging, sizeof(GroupSeg) * s->nseg,
@@ -207,7 +211,20 @@ croft_status group_graph_add(GroupState* s, cudaGraph_t g, float isign) {
             kp.sharedMemBytes = (unsigned)L.smem;
             kp.kernelParams = params;
             cudaGraphNode_t kn;
-            if (cudaGraphAddKernelNode(&kn, g, prev.data(), prev.size(), &kp) != cudaSuccess) return CROFT_ERR_CUDA;
+            if (p == 0 || !pdl) {
+                if (cudaGraphAddKernelNode(&kn, g, prev.data(), prev.size(), &kp) != cudaSuccess) return CROFT_ERR_CUDA;
+            } else {
+                if (cudaGraphAddKernelNode(&kn, g, nullptr, 0, &kp) != cudaSuccess) return CROFT_ERR_CUDA;
+                std::vector<cudaGraphNode_t> to(prev.size(), kn);
+                std::vector<cudaGraphEdgeData> ed(prev.size());
+                for (cudaGraphEdgeData& e : ed) {
+                    memset(&e, 0, sizeof(e));
+                    e.from_port = cudaGraphKernelNodePortProgrammatic;
+                    e.type = cudaGraphDependencyTypeProgrammatic;
+                }
+                if (cudaGraphAddDependencies(g, prev.data(), to.data(), ed.data(), prev.size()) != cudaSuccess)
+                    return CROFT_ERR_CUDA;
+            }
             cur.push_back(kn);
         }
         if (!cur.empty()) prev = cur;

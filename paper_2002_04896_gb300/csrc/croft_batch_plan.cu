@@ -49,7 +49,7 @@ struct GroupState;  // croft_batch_group.cu
 croft_status group_state_build(const std::vector<int>& dims, const std::vector<int>& pgrid, GroupState** out);
 void group_state_destroy(GroupState* s);
 void group_state_fill(GroupState* s, void* const* in, void* const* out);
-croft_status group_graph_add(GroupState* s, cudaGraph_t g, float isign);
+croft_status group_graph_add(GroupState* s, cudaGraph_t g, float isign, bool pdl);
 int group_state_launches(const GroupState* s);
 
 struct BatchState {
@@ -236,7 +236,8 @@ static croft_status build_graphs(BatchState* b) {
         if (cudaGraphCreate(&g, 0) != cudaSuccess) return CROFT_ERR_CUDA;
         b->graph[d] = g;
         if (b->mode == CROFT_BATCH_GROUPED) {
-            croft_status st = group_graph_add(b->group, g, isign);
+            const char* pdl_env = getenv("CROFT_PDL");  // 0: ordinary graph edges between the passes
+            croft_status st = group_graph_add(b->group, g, isign, !(pdl_env && pdl_env[0] == '0'));
             if (st != CROFT_OK) return st;
             if (cudaGraphInstantiate(&b->gexec[d], g, 0) != cudaSuccess) return CROFT_ERR_CUDA;
             continue;

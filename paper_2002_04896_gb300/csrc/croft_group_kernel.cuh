@@ -40,10 +40,14 @@ __global__ void __launch_bounds__(256) croft_group_kernel(const __grid_constant_
     extern __shared__ __align__(16) unsigned char smem_raw[];
     float2* stw = reinterpret_cast<float2*>(smem_raw);
     float2* sbuf = stw + TW_PAD;
+    pdl_allow_dependents();
     if (croft_make_sched(N).count > 1)
         for (int i = threadIdx.x; i < N - 1; i += blockDim.x) stw[i] = A.tw[i];
+    // (the segment table is uploaded before the first pass starts; the grid is written by
+    // the previous pass, whose launches reach this one over programmatic graph edges)
     const GroupSeg S = A.segs[A.cta_seg[blockIdx.x]];
     const long long tile = (long long)blockIdx.x - S.first_tile;
+    pdl_wait();
     if constexpr (LAYOUT == LAYOUT_ROW) {
         const int c = threadIdx.x / T;
         const int lane = threadIdx.x - c * T;
