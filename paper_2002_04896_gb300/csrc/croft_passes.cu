@@ -44,6 +44,7 @@ bool shape_pass(PassLaunch& L, int layout, int n, long long M, long long ncols, 
         int W = 16;
         if (tc) {
             while (W * 2 * T <= 256) W *= 2;
+            if (croft_col_narrow(n, (int)es, M * es)) W = kColNarrowWidth;  // (two 128-butterfly groups)
         } else {
             W = croft_col_width_at(n, (int)es, M * es);  // a width the kernels are built for
         }
