@@ -20,7 +20,8 @@ static pass_fn col_kernel(int w) {
     constexpr int W = croft_col_width(N, 8);
     if constexpr (croft_threads_per_pencil(N) == 32 && W != kColNarrowWidth)
         if (w == kColNarrowWidth)
-            return croft_pass_kernel_bounded<LAYOUT_COL, N, float2, kColNarrowWidth, kColNarrowMinb, kColNarrowWidth * 32>;
+            return croft_pass_kernel_bounded<LAYOUT_COL, N, float2, kColNarrowWidth, croft_col_narrow_minb(N),
+                                             kColNarrowWidth * 32>;
     if (w != W) return nullptr;
     if constexpr (croft_col_minb(N, 8) > 1) return croft_pass_kernel_bounded<LAYOUT_COL, N, float2, W, croft_col_minb(N, 8)>;
     else if constexpr (croft_pass_minb(N, 8) > 0)
