@@ -180,10 +180,10 @@ CROFT_HD constexpr int croft_col_minb(int n, int es) { return (es == 8 && croft_
 
 // Short-stride column passes of complex64 32-thread pencils (the y pass: the axis's
 // elements at most 16 KB apart) take 8-column, 256-thread tiles bounded to five CTAs
-// per SM instead (48 registers, 0-52 bytes of spills; croft_col_narrow_minb): 512^3 y pass 455 -> 414 us,
-// 320^3 121 -> 115 us, 360-point y pass of 384x360x320 162 -> 160 us, 480^3 330 ->
-// 332 us.  Across the x pass's megabyte strides the 64-byte row pieces lose (512^3
-// 487 -> 649 us), so that pass keeps croft_col_width's 16 columns.
+// per SM instead (48 registers, 0-52 bytes of spills; croft_col_narrow_minb): 512^3 y
+// pass 455 -> 414 us, 320^3 121 -> 115 us, 360-point y pass of 384x360x320 162 -> 160
+// us, 480^3 330 -> 332 us.  Across the x pass's megabyte strides the 64-byte row pieces
+// lose (512^3 487 -> 649 us), so that pass keeps croft_col_width's 16 columns.
 constexpr int kColNarrowWidth = 8;
 // CTAs per SM the narrow kernel's registers must allow: five (48 registers), except where
 // four (64) measured faster - the lengths whose five-CTA build spills most, and 480.  y pass
