@@ -733,6 +733,7 @@ def run_croft(args):
                        "passes_per_direction": npass, "schedule": args.schedule, "plan": plan_desc},
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                          "frac": achieved / peak, "traffic": traffic, "kernel": dom_key,
+                         "kernel_source_sha": kernel_source_sha(),
                          "peak_source": peak_kind, "alg_bytes_per_launch": alg_bytes,
                          "pass_ms": pass_ms, "dominant_ms_in_timed_step": dom_ms_in_step,
                          "achieved_per_pass_events": achieved_events,

@@ -13,6 +13,7 @@
 // barrier between the reads and the writes of the stage (needed when the
 // writes overwrite data other threads still have to read).
 #pragma once
+#include <type_traits>
 #include <cooperative_groups.h>
 
 #include "croft_butterflies.cuh"
@@ -122,6 +123,10 @@ using SmemCol = SmemColT<float2>;
 template <class C, int W>
 struct SmemColFixed {
     using value_type = C;
+    // Rows of 64 bytes cover half of the banks: a first stage with an even radix R0 then
+    // writes rows R0*b + j of consecutive butterflies b all on one half, unless odd
+    // butterflies store their pairs of outputs in swapped order (fft_stage_s).
+    static constexpr bool kPairSwap = W * (int)sizeof(C) == 64;
     C* s;  // tile + c
     __device__ __forceinline__ C load(int a) const { return s[a * W]; }
     __device__ __forceinline__ void store(int a, C v) const { s[a * W] = v; }
@@ -171,6 +176,12 @@ struct Tc16Sched {
 // ---------------------------------------------------------------------------
 // the stage
 // ---------------------------------------------------------------------------
+// Whether a destination wants the pair-swapped store order of a first stage (kPairSwap).
+template <class D, class = void>
+struct PairSwapStores : std::false_type {};
+template <class D>
+struct PairSwapStores<D, std::void_t<decltype(D::kPairSwap)>> : std::bool_constant<D::kPairSwap> {};
+
 template <class SchedT, int S, int T, class Src, class Mid, class Dst>
 __device__ __forceinline__ void fft_stage_s(const Src& src, const Mid& mid, const Dst& dst,
                                             const typename Src::value_type* stw, int lane, bool ok) {
@@ -203,8 +214,21 @@ __device__ __forceinline__ void fft_stage_s(const Src& src, const Mid& mid, cons
             }
             dft<R>(v[q]);
             const int o = (b - k) * R + k;
+            if constexpr (P == 1 && R % 2 == 0 && PairSwapStores<Dst>::value) {
+                // same stores, odd butterflies take each pair (j, j+1) in swapped order: the
+                // rows one instruction writes then alternate between the two bank halves
+                const int odd = b & 1;
 #pragma unroll
-            for (int j = 0; j < R; ++j) dst.store(o + j * P, v[q][j]);
+                for (int j = 0; j < R; j += 2) {
+                    const C first = odd ? v[q][j + 1] : v[q][j];
+                    const C second = odd ? v[q][j] : v[q][j + 1];
+                    dst.store(o + odd + j, first);
+                    dst.store(o + 1 - odd + j, second);
+                }
+            } else {
+#pragma unroll
+                for (int j = 0; j < R; ++j) dst.store(o + j * P, v[q][j]);
+            }
         }
     }
 }
