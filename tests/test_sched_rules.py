@@ -1,0 +1,146 @@
+"""Host checks of the compile-time schedule and tile rules of the pass kernels
+(``csrc/croft_sched.h``), compiled with the host C++ compiler (CPU only).
+
+The kernels, the planner and the twiddle-table builder all take their radix
+schedules, threads per pencil, column-tile widths and launch bounds from this
+one header; these tests pin the rules it states for every supported length:
+the schedule is a factorisation into the butterfly set with the first-stage
+rule, the tiles fit the launch and shared-memory limits, and the narrow
+8-column tile is chosen exactly for short-stride complex64 passes of 32-thread
+pencils.
+"""
+
+import math
+import os
+import shutil
+import subprocess
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+CSRC = os.path.join(ROOT, "paper_2002_04896_gb300", "csrc")
+RADICES = {2, 3, 4, 5, 8, 9, 15, 16}
+
+PROGRAM = r"""
+#include <cstdio>
+#include <initializer_list>
+#include "croft_sched.h"
+int main() {
+    for (int n = 2; n <= 4096; ++n) {
+        int m = n;
+        for (int p : {2, 3, 5})
+            while (m % p == 0) m /= p;
+        if (m != 1) continue;
+        for (int layout = 0; layout < 2; ++layout) {
+            const CroftSched s = croft_pass_sched(n, layout, 8);
+            std::printf("S %d %d", n, layout);
+            for (int i = 0; i < s.count; ++i) std::printf(" %d", s.r[i]);
+            std::printf("\n");
+        }
+        std::printf("T %d %d\n", n, croft_threads_per_pencil(n));
+        for (int es : {8, 16})
+            std::printf("W %d %d %d %d %d\n", n, es, croft_col_width(n, es), croft_col_width_at(n, es, 4096),
+                        croft_col_width_at(n, es, 1 << 21));
+        std::printf("B %d %d %d %d\n", n, croft_col_minb(n, 8), croft_pass_minb(n, 8), croft_col_narrow_minb(n));
+    }
+    return 0;
+}
+"""
+
+
+@pytest.fixture(scope="module")
+def rules(tmp_path_factory):
+    cxx = shutil.which("g++") or shutil.which("c++")
+    if not cxx:
+        pytest.skip("no host C++ compiler")
+    d = tmp_path_factory.mktemp("sched")
+    src, exe = d / "rules.cpp", d / "rules"
+    src.write_text(PROGRAM)
+    subprocess.run([cxx, "-std=c++17", "-O1", "-I", CSRC, str(src), "-o", str(exe)], check=True)
+    out = subprocess.run([str(exe)], check=True, capture_output=True, text=True).stdout
+    r = {"S": {}, "T": {}, "W": {}, "B": {}}
+    for line in out.splitlines():
+        tag, *v = line.split()
+        v = [int(a) for a in v]
+        if tag == "S":
+            r["S"][(v[0], v[1])] = v[2:]
+        elif tag == "T":
+            r["T"][v[0]] = v[1]
+        elif tag == "W":
+            r["W"][(v[0], v[1])] = v[2:]
+        else:
+            r["B"][v[0]] = v[1:]
+    return r
+
+
+def test_every_length_is_covered(rules):
+    assert len(rules["T"]) == 136  # 2 <= n <= 4096 of the form 2^a 3^b 5^c
+
+
+def test_schedules_factorise_into_the_butterfly_set(rules):
+    for (n, layout), rs in rules["S"].items():
+        assert math.prod(rs) == n, (n, layout, rs)
+        assert set(rs) <= RADICES, (n, layout, rs)
+        assert len(rs) <= 8
+
+
+def test_first_stage_rule(rules):
+    """The first stage (the one that loads from HBM) takes a radix whose butterflies give
+    a thread at most emax elements whenever the schedule has one."""
+    for (n, layout), rs in rules["S"].items():
+        t = rules["T"][n]
+        emax = 16 if n <= 1024 else 32
+        per_thread = [-(-(n // r) // t) * r for r in rs]
+        if any(e <= emax for e in per_thread):
+            assert per_thread[0] <= emax, (n, layout, rs, t)
+
+
+def test_power_of_two_split(rules):
+    """Row passes split the power-of-two part greedily into radix-16 stages; column
+    passes of complex64 32-thread pencils split it into near-equal stages."""
+    for (n, layout), rs in rules["S"].items():
+        pow2 = sorted((r for r in rs if r in (2, 4, 8, 16)), reverse=True)
+        a = int(math.log2(math.prod(pow2))) if pow2 else 0
+        if a == 0:
+            continue
+        even = layout == 1 and rules["T"][n] == 32
+        if even:
+            k = -(-a // 4)
+            sizes = sorted((int(math.log2(r)) for r in pow2), reverse=True)
+            assert len(sizes) == k and max(sizes) - min(sizes) <= 1, (n, rs)
+        else:
+            assert [int(math.log2(r)) for r in pow2][:-1] == [4] * (len(pow2) - 1), (n, rs)
+
+
+def test_threads_per_pencil(rules):
+    for n, t in rules["T"].items():
+        assert t == 1 << (t.bit_length() - 1) and t <= 32 or t % 32 == 0, (n, t)
+        emax = 16 if n <= 1024 else 32
+        assert t * emax >= n, (n, t)
+
+
+def test_column_tiles_fit_the_launch_and_shared_memory(rules):
+    for (n, es), (w, w_short, w_long) in rules["W"].items():
+        t = rules["T"][n]
+        tw_pad = (n + 1) // 2 * 2
+        for width in (w, w_short, w_long):
+            assert width >= 1 and width * t <= 512, (n, es, width, t)
+            fits = (tw_pad + n * width) * es <= 100 * 1024
+            assert fits or width == 1, (n, es, width)  # narrowed down to one column at most
+            assert fits or es == 16, (n, es, width)  # every complex64 length fits
+        assert w_long == w, (n, es)  # megabyte strides keep the default width
+        narrow = es == 8 and t == 32
+        assert (w_short == 8 and w_short != w) == narrow, (n, es, w, w_short)
+        if not narrow:
+            assert w_short == w
+
+
+def test_launch_bounds(rules):
+    for n, (col_minb, pass_minb, narrow_minb) in rules["B"].items():
+        t = rules["T"][n]
+        assert col_minb == (3 if t == 32 else 1), n
+        assert pass_minb == (5 if n == 256 else 0), n
+        assert narrow_minb in (4, 5), n
+        assert (narrow_minb == 4) == (n in (480, 486, 500)), n
+        # registers a thread may keep under the bound: 48 for five 256-thread CTAs, 64 for four
+        assert 65536 // (narrow_minb * 256) >= 48
