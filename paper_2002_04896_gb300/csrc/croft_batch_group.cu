@@ -222,8 +222,11 @@ croft_status group_graph_add(GroupState* s, cudaGraph_t g, float isign, bool pdl
                     e.from_port = cudaGraphKernelNodePortProgrammatic;
                     e.type = cudaGraphDependencyTypeProgrammatic;
                 }
-                if (cudaGraphAddDependencies(g, prev.data(), to.data(), ed.data(), prev.size()) != cudaSuccess)
-                    return CROFT_ERR_CUDA;
+                if (cudaGraphAddDependencies(g, prev.data(), to.data(), ed.data(), prev.size()) != cudaSuccess) {
+                    cudaGetLastError();  // programmatic edges refused: plain edges (the kernel's wait returns at once)
+                    if (cudaGraphAddDependencies(g, prev.data(), to.data(), nullptr, prev.size()) != cudaSuccess)
+                        return CROFT_ERR_CUDA;
+                }
             }
             cur.push_back(kn);
         }
