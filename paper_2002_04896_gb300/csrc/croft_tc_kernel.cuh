@@ -27,6 +27,7 @@
 // the stage is in registers before the tile is overwritten, and every MMA has
 // completed (mbarrier) before the outputs are written back into it.
 #pragma once
+#include <type_traits>
 #include <cuda_bf16.h>
 
 #include "croft_fft_core.cuh"
@@ -172,8 +173,22 @@ __device__ __forceinline__ void fft_stage_tc16(const Src& src, const Dst& dst, c
     if (ok) {
         const int k = (P == 1) ? 0 : b % P;
         const int o = (b - k) * 16 + k;
+        bool swap = false;
+        if constexpr (P == 1 && std::is_same<Dst, SmemCol>::value) swap = dst.W == 8;  // 64-byte rows
+        if (swap) {
+            // odd butterflies store each output pair (j, j+1) in swapped order, so the rows one
+            // store instruction writes alternate between the two bank halves
+            const int odd = b & 1;
 #pragma unroll
-        for (int j = 0; j < 16; ++j) dst.store(o + j * P, make_float2(d[j], d[16 + j]));
+            for (int j = 0; j < 16; j += 2) {
+                const float2 v0 = make_float2(d[j], d[16 + j]), v1 = make_float2(d[j + 1], d[17 + j]);
+                dst.store(o + odd + j, odd ? v1 : v0);
+                dst.store(o + 1 - odd + j, odd ? v0 : v1);
+            }
+        } else {
+#pragma unroll
+            for (int j = 0; j < 16; ++j) dst.store(o + j * P, make_float2(d[j], d[16 + j]));
+        }
     }
 }
 
