@@ -1,21 +1,25 @@
 #!/usr/bin/env python3
-"""Benchmark: 3D C2C FFT (forward + backward) of a 256^3 PME-shaped complex64 grid.
+"""Benchmark: 3D C2C FFT (forward + backward) of a 512^3 PME-shaped complex64 grid,
+FP32 CUDA-core passes against split-precision tensor-core radix-16 stages.
 
-One step = one forward and one backward transform of the whole grid through
-the C ABI (libcroft.so), i.e. every pass of the hot path.  Metric: GFLOP/s with
-the nominal count 5 N log2 N per direction.
+One step = one forward and one backward transform of the whole grid through the
+C ABI (libcroft.so), i.e. every pass of the hot path.  Metric: GFLOP/s with the
+nominal count 5 N log2 N per direction.  `value` is the FP32 path; the line's
+`tc` object times the tensor-core path (CROFT_C2C_F32_TC_BF16X3) with the same
+protocol on the same input.  After the timed regions both paths' forward
+results and round trips are compared with the FP64 oracle on the full grid
+(`errors`).
 
-Timing: plan outside the timed region; W warm-up steps; then K steps, each
-preceded by an L2 flush (a write of a buffer twice the L2 size, outside the
-timed events); each transform is bracketed by CUDA events on the stream it runs
-on and the step time is the sum of the two.  The dominant pass kernel is timed
-by the plan's own per-pass events inside the same steps.
+Timing: plans outside the timed regions; W warm-up steps; then K steps per
+path, each preceded by an L2 flush (a write of a buffer twice the L2 size,
+outside the timed events); each step is bracketed by CUDA events on the stream
+it runs on.  The dominant pass kernel's duration comes from the plan's per-pass
+events over K more steps run right after the timed ones.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl croft|reference]
 
 With N > 1 (torchrun) every rank runs an independent replica of the workload
-(the single-grid transform has no data-parallel shard on one box) and value is
-the sum over ranks; the time is the max over ranks.
+and value is the sum over ranks; the time is the max over ranks.
 
 --impl reference times the FP64 CPU oracle (the only reference this method has)
 on the host cores, on a bounded sample of the same workload.
@@ -37,10 +41,15 @@ import time
 ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
-SHAPE = (256, 256, 256)
-WORKLOAD = "pme256: 256x256x256 complex64 C2C forward+backward, 200k +-1 charges spread by order-4 B-splines, seed 1"
+CONFIG = "pme512"
+SHAPE = (512, 512, 512)
+WORKLOAD = ("pme512: 512x512x512 complex64 C2C forward+backward, 8M +-1 charges (net zero, iid uniform positions) "
+            "spread by order-4 B-splines, seed 4; FP32 CUDA-core passes (value) and split-precision tensor-core "
+            "radix-16 stages (tc) on the same input")
 METRIC = "3D C2C FFT GFLOP/s (5N log2 N), % of HBM roofline, TC vs FP32 at fixed error"
 HBM_FALLBACK_GBS = 6800.0
+FP32_TOL_PER_LOG2 = 2e-6  # rel L2 bar of the FP32 path: 2e-6 * log2(N)
+TC_TOL = 3e-5             # rel L2 bar of the tensor-core path
 
 
 def nominal_flops(shape) -> float:
@@ -62,20 +71,24 @@ def measured_peaks():
 # taken with ncu stays valid while these files are unchanged.
 PASS_KERNEL_SOURCES = ("croft_butterflies.cuh", "croft_fft_core.cuh", "croft_internal.h", "croft_kernels.cu",
                        "croft_pass_kernel.cuh", "croft_passes.cu", "croft_row_layouts.h",
-                       "croft_sched.h", "croft_sizes.h")
+                       "croft_sched.h", "croft_sizes.h", "croft_ring_kernel.cuh", "croft_ring.cu")
+TC_KERNEL_SOURCES = PASS_KERNEL_SOURCES + ("croft_tc_kernel.cuh", "croft_tc.cu")
 
 
-def kernel_source_sha() -> str:
+def kernel_source_sha(names=PASS_KERNEL_SOURCES) -> str:
     h = hashlib.sha256()
     csrc = os.path.join(ROOT, "paper_2002_04896_gb300", "csrc")
-    for name in PASS_KERNEL_SOURCES:
-        with open(os.path.join(csrc, name), "rb") as f:
+    for name in names:
+        p = os.path.join(csrc, name)
+        if not os.path.exists(p):
+            continue
+        with open(p, "rb") as f:
             h.update(name.encode())
             h.update(f.read())
     return h.hexdigest()[:16]
 
 
-def ncu_traffic(kernel_key: str):
+def ncu_traffic(kernel_key: str, names=PASS_KERNEL_SOURCES):
     """DRAM bytes per launch from the committed ncu summary, if it was taken on the current kernel source."""
     p = os.path.join(ROOT, "profiles", "ncu_dram_traffic.json")
     try:
@@ -84,7 +97,7 @@ def ncu_traffic(kernel_key: str):
     except Exception:  # noqa: BLE001
         return None
     ent = d.get(kernel_key)
-    if not ent or ent.get("src_sha") != kernel_source_sha():
+    if not ent or ent.get("src_sha") != kernel_source_sha(names):
         return None
     return float(ent["dram_bytes_per_launch"])
 
@@ -195,24 +208,29 @@ def cpu_oracle_step(x, sample_planes=None):
     return 2 * nominal_flops(x.shape) * frac
 
 
+def oracle_sample_planes(x, budget_s: float):
+    """Planes per sampled oracle step so that one step takes about budget_s (timed on 8 planes)."""
+    t0 = time.perf_counter()
+    cpu_oracle_step(x, 8)
+    t8 = max(1e-3, time.perf_counter() - t0)
+    s = int(8 * budget_s / t8)
+    return max(1, min(x.shape[0], s))
+
+
 def run_reference(args):
     world, rank, _ = dist_env()
     if rank != 0:
         return 0
-    import numpy as np
-
     import synthetic_inputs as S
 
-    x = S.config_input("pme256")
+    x = S.config_input(CONFIG)
     cores = os.cpu_count()
-    # the whole step unless (steps + warmup) full steps would exceed ~3 minutes; then a
-    # fixed fraction of the pencils of every axis per step
-    t0 = time.perf_counter()
-    cpu_oracle_step(x, None)
-    t_full = time.perf_counter() - t0
-    sample = None
-    if t_full * (args.steps + args.warmup) > 180.0:
-        sample = max(1, int(SHAPE[0] * 180.0 / (t_full * (args.steps + args.warmup))))
+    # each step a bounded sample of the workload (a fixed fraction of the pencils of every
+    # axis), sized so that all (warm-up + timed) steps take about --reference-budget-s seconds
+    per_step = args.reference_budget_s / (args.steps + args.warmup)
+    sample = oracle_sample_planes(x, per_step)
+    if sample >= SHAPE[0]:
+        sample = None
     for _ in range(args.warmup - 1):
         cpu_oracle_step(x, sample)
     t0 = time.perf_counter()
@@ -223,7 +241,7 @@ def run_reference(args):
     val = fl / dt / 1e9
     part = "all" if sample is None else f"{sample}/{SHAPE[0]}"
     desc = (f"FP64 oracle (numpy matmul per-axis DFT), forward+backward on {part} of the pencils "
-            f"of each axis of the pme256 grid per step")
+            f"of each axis of the {CONFIG} grid per step")
     line = {
         "impl": "reference", "metric": METRIC, "value": val, "unit": "GFLOP/s", "n_gpus": args.gpus,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": dt / args.steps * 1e3,
@@ -278,14 +296,92 @@ def time_transform(croft, torch, stream, flush, plan, run_fwd, run_bwd, reps=5, 
     return statistics.median(fw), statistics.median(bw), pass_ms
 
 
-ROW_NAMES = ("pme480_fp32", "pme384x360x320_fp32", "pme512_fp32", "pme512_tc_bf16x3", "pme256_convolve",
-             "f64_128", "f64_1024", "batch96")
+AXIS_NAMES = {3: ["z", "y", "x"], 2: ["yz", "x"], 1: ["yz"]}
 
 
-def measure_rows(croft, torch, dev, stream, flush, peak, only=None):  # noqa: PLR0915
-    """The other hot-path rows, timed on device-generated data (timing does not depend on values):
-    non-power-of-two meshes, FP32 vs tensor-core 512^3 (with the round-trip error of each),
-    and the 96-grid batch (one persistent launch vs per-grid plans)."""
+def roofline(pass_ms, ms_step, shape, peak, peak_kind, key_suffix="", sources=PASS_KERNEL_SOURCES):
+    """Roofline of the dominant pass: its algorithmic bytes (one read + one write of the grid,
+    16 N) over its duration inside the timed steps (its share of the per-pass events times the
+    timed time of one transform)."""
+    n_total = math.prod(shape)
+    npass = len(pass_ms)
+    dom = max(range(npass), key=lambda i: pass_ms[i])
+    names = AXIS_NAMES.get(npass, [f"p{i}" for i in range(npass)])
+    alg_bytes = 16.0 * n_total
+    achieved_events = alg_bytes / (pass_ms[dom] * 1e-3) / 1e9
+    dom_ms_in_step = pass_ms[dom] / sum(pass_ms) * (ms_step / 2)
+    achieved = alg_bytes / (dom_ms_in_step * 1e-3) / 1e9
+    key = f"pass_{names[dom]}_{'x'.join(map(str, shape))}{key_suffix}"
+    return {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+            "traffic": ncu_traffic(key, sources), "kernel": key, "kernel_source_sha": kernel_source_sha(sources),
+            "peak_source": peak_kind, "alg_bytes_per_launch": alg_bytes, "pass_ms": pass_ms,
+            "dominant_ms_in_timed_step": dom_ms_in_step, "achieved_per_pass_events": achieved_events,
+            "frac_per_pass_events": achieved_events / peak,
+            "kernel_timing": "per-pass shares from CUDA events on the launch stream after every pass, over "
+                             "the steps run right after the timed ones; absolute duration = share x the timed "
+                             "time of one transform (an event between two passes adds a gap and stops the next "
+                             "pass from launching early, so the timed steps carry events only at their ends; "
+                             "achieved_per_pass_events is the same figure from the per-pass events alone)"}
+
+
+def errors_vs_oracle(x_h, y_h, z_h, ref, slab: int = 32):
+    """Errors of one path's results against the FP64 oracle, accumulated in float64 over x-slabs.
+
+    rel_l2_fwd       ||Y - Y_ref|| / ||Y_ref||            (the bar: 2e-6 log2 N FP32, 3e-5 TC)
+    max_rel_fwd      max |Y - Y_ref| / max |Y_ref|          (per element, scaled by the largest output)
+    rel_l2_fwd_high_k  the same rel L2 over the outputs whose normalised frequency
+                     |k| = sqrt(sum_a (m_a / (K_a/2))^2) >= 1 (m_a the signed frequency): the outer
+                     half of the spectrum, where a PME grid has little energy
+    rel_l2_roundtrip ||B(F(x)) - N x|| / ||N x||
+    """
+    import numpy as np
+
+    nx, ny, nz = x_h.shape
+    n_total = x_h.size
+
+    def sfreq(k):
+        m = np.arange(k, dtype=np.float64)
+        m = np.where(m <= k // 2, m, m - k)
+        return (m / (k / 2.0)) ** 2 if k > 1 else np.zeros(1)
+
+    fy, fz = sfreq(ny), sfreq(nz)
+    fx = sfreq(nx)
+    acc = dict(num=0.0, den=0.0, hnum=0.0, hden=0.0, rnum=0.0, rden=0.0, maxerr=0.0, maxref=0.0)
+    for x0 in range(0, nx, slab):
+        sl = slice(x0, min(nx, x0 + slab))
+        r = ref[sl]
+        d = y_h[sl].astype(np.complex128) - r
+        e2 = d.real ** 2 + d.imag ** 2
+        r2 = r.real ** 2 + r.imag ** 2
+        acc["num"] += float(e2.sum())
+        acc["den"] += float(r2.sum())
+        acc["maxerr"] = max(acc["maxerr"], float(np.sqrt(e2.max())))
+        acc["maxref"] = max(acc["maxref"], float(np.sqrt(r2.max())))
+        band = (fx[sl, None, None] + fy[None, :, None] + fz[None, None, :]) >= 1.0
+        acc["hnum"] += float(e2[band].sum())
+        acc["hden"] += float(r2[band].sum())
+        xr = x_h[sl].astype(np.complex128) * n_total
+        dr = z_h[sl].astype(np.complex128) - xr
+        acc["rnum"] += float((dr.real ** 2 + dr.imag ** 2).sum())
+        acc["rden"] += float((xr.real ** 2 + xr.imag ** 2).sum())
+
+    def q(a, b):
+        return math.sqrt(a / b) if b > 0 else math.sqrt(a)
+
+    return {"rel_l2_fwd": q(acc["num"], acc["den"]),
+            "max_rel_fwd": acc["maxerr"] / acc["maxref"] if acc["maxref"] > 0 else acc["maxerr"],
+            "rel_l2_fwd_high_k": q(acc["hnum"], acc["hden"]),
+            "rel_l2_roundtrip": q(acc["rnum"], acc["rden"])}
+
+
+ROW_NAMES = ("pme256_fp32", "pme480_fp32", "pme384x360x320_fp32", "pme256_convolve", "f64_128", "f64_1024",
+             "batch96")
+
+
+def measure_rows(croft, torch, dev, stream, flush, peak, peak_kind, only=None):  # noqa: PLR0915
+    """The other hot-path rows: the 256^3 PME grid (real input), non-power-of-two meshes on
+    device-generated data (timing does not depend on values), the fused PME convolution,
+    complex128 at the paper's sizes and the 96-grid batch in every schedule."""
     import numpy as np
 
     import synthetic_inputs as S
@@ -301,41 +397,37 @@ def measure_rows(croft, torch, dev, stream, flush, peak, only=None):  # noqa: PL
     def want(name):
         return only is None or name in only
 
-    for name, shape, dtype in (("pme480_fp32", (480, 480, 480), 0), ("pme384x360x320_fp32", (384, 360, 320), 0),
-                               ("pme512_fp32", (512, 512, 512), 0), ("pme512_tc_bf16x3", (512, 512, 512), 1)):
+    for name, shape in (("pme256_fp32", (256, 256, 256)), ("pme480_fp32", (480, 480, 480)),
+                        ("pme384x360x320_fp32", (384, 360, 320))):
         if not want(name):
             continue
-        x = grid(shape)
+        x = torch.from_numpy(S.config_input("pme256")).to(dev) if name == "pme256_fp32" else grid(shape)
         y = torch.empty_like(x)
         z = torch.empty_like(x)
         n = math.prod(shape)
-        with croft.Plan(*shape, dtype=dtype) as p:
+        with croft.Plan(*shape) as p:
             croft.croft_plan_set_timing(p.handle, True)
             sh = stream.cuda_stream
             f_ms, b_ms, pass_ms = time_transform(
                 croft, torch, stream, flush, p.handle,
                 lambda: croft.croft_exec_forward(p.handle, x, y, sh),
-                lambda: croft.croft_exec_backward(p.handle, y, z, sh))
+                lambda: croft.croft_exec_backward(p.handle, y, z, sh), reps=10)
             desc = p.describe()
         stream.synchronize()
         rt = float(torch.linalg.vector_norm((z - n * x).flatten()) / torch.linalg.vector_norm((n * x).flatten()))
         t = f_ms + b_ms
-        cufft = None
-        if dtype == 0:  # library context: cuFFT through torch.fft, same protocol
-            del z
-            cf, cb, _ = time_transform(croft, torch, stream, flush, None,
-                                       lambda: torch.fft.fftn(x, norm="backward", out=y),
-                                       lambda: torch.fft.ifftn(y, norm="forward"))
-            cufft = {"ms_fwd": cf, "ms_bwd": cb, "gflops": 2 * nominal_flops(shape) / ((cf + cb) * 1e-3) / 1e9}
-            z = None
-        dom = max(range(len(pass_ms)), key=lambda i: pass_ms[i])
+        del z
+        cf, cb, _ = time_transform(croft, torch, stream, flush, None,
+                                   lambda: torch.fft.fftn(x, norm="backward", out=y),
+                                   lambda: torch.fft.ifftn(y, norm="forward"))
+        cufft = {"ms_fwd": cf, "ms_bwd": cb, "gflops": 2 * nominal_flops(shape) / ((cf + cb) * 1e-3) / 1e9}
         rows[name] = {"shape": list(shape), "ms_fwd": f_ms, "ms_bwd": b_ms,
                       "gflops": 2 * nominal_flops(shape) / (t * 1e-3) / 1e9,
                       "hbm_frac_whole_transform": (32.0 * n / (t * 1e-3) / 1e9) / peak,
-                      "pass_ms": pass_ms, "dominant_pass_gbs": 16.0 * n / (pass_ms[dom] * 1e-3) / 1e9,
-                      "dominant_pass_frac": (16.0 * n / (pass_ms[dom] * 1e-3) / 1e9) / peak,
-                      "roundtrip_rel_l2": rt, "plan": desc, "cufft_torch_fftn_context": cufft}
-        del x, y, z
+                      "roofline": roofline(pass_ms, t, shape, peak, peak_kind),
+                      "roundtrip_rel_l2": rt, "plan": desc, "cufft_torch_fftn_context": cufft,
+                      "input": "pme256 (seed 1, 200k charges)" if name == "pme256_fp32" else "device uniform noise"}
+        del x, y
     if want("pme256_convolve"):
         # PME reciprocal-space convolution B(G * F(x)) on 256^3 with the smooth-PME influence function:
         # croft_exec_convolve (last-axis forward * G * backward fused) vs forward, a torch multiply, backward
@@ -444,7 +536,7 @@ def measure_rows(croft, torch, dev, stream, flush, peak, only=None):  # noqa: PL
         err = max(float(torch.linalg.vector_norm((z - math.prod(d) * x).flatten()) /
                         torch.linalg.vector_norm((math.prod(d) * x).flatten())) for d, x, z in zip(dims, xs, zs))
         brow["roundtrip_rel_l2_max"] = err
-        # the autotuned plan (CROFT_BATCH_AUTO): times the four schedules on scratch buffers at
+        # the autotuned plan (CROFT_BATCH_AUTO): times the schedules on scratch buffers at
         # creation (a fresh cache file, so it measures) and keeps the fastest
         import tempfile
         with tempfile.TemporaryDirectory() as td:
@@ -490,9 +582,10 @@ def library_context(torch, x, flush, stream, x_h, flops_step, skip_cpu):
         stream.synchronize()
         if i >= 3:
             times.append(a.elapsed_time(b))
+    del yf
     ms = statistics.median(times)
     out["cufft_torch_fftn"] = {"ms_per_step": ms, "gflops": flops_step / (ms * 1e-3) / 1e9,
-                               "note": "torch.fft.fftn + ifftn(norm='forward') on the same 256^3 complex64 grid"}
+                               "note": f"torch.fft.fftn + ifftn(norm='forward') on the same {CONFIG} complex64 grid"}
     if not skip_cpu:
         try:
             import numpy as np
@@ -510,12 +603,60 @@ def library_context(torch, x, flush, stream, x_h, flops_step, skip_cpu):
                 sec = (time.perf_counter() - t0) / reps
                 out[f"scipy_fft_{name}"] = {"ms_per_step": sec * 1e3, "gflops": flops_step / sec / 1e9,
                                              "cores": os.cpu_count()}
+                del xc
         except Exception as e:  # noqa: BLE001 - context only
             out["scipy_fft"] = {"unavailable": str(e)[:200]}
     return out
 
 
-def run_croft(args):
+class Arm:
+    """One path (plan) of the headline: warm-up, timed steps, per-pass steps."""
+
+    def __init__(self, croft, torch, stream, flush, plan, x, y, z):
+        self.croft, self.torch, self.stream, self.flush = croft, torch, stream, flush
+        self.plan, self.x, self.y, self.z = plan, x, y, z
+        self.sh = stream.cuda_stream
+        self.rec = []
+        self.rec_pp = []
+
+    def step(self, record, fills=1):
+        """One forward + backward; device time between two events (none between the passes)."""
+        torch, croft, stream = self.torch, self.croft, self.stream
+        with torch.cuda.stream(stream):
+            for _ in range(fills):
+                self.flush.fill_(1.0)
+            e = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
+            e[0].record(stream)
+            croft.croft_exec_forward(self.plan.handle, self.x, self.y, self.sh)
+            croft.croft_exec_backward(self.plan.handle, self.y, self.z, self.sh)
+            e[1].record(stream)
+        stream.synchronize()
+        if record is not None:
+            record.append(e[0].elapsed_time(e[1]))
+
+    def step_per_pass(self):
+        """The same step with an event after every pass (per-kernel durations)."""
+        torch, croft, stream = self.torch, self.croft, self.stream
+        with torch.cuda.stream(stream):
+            self.flush.fill_(1.0)
+            croft.croft_exec_forward(self.plan.handle, self.x, self.y, self.sh)
+        pf = croft.croft_plan_pass_times(self.plan.handle)
+        with torch.cuda.stream(stream):
+            croft.croft_exec_backward(self.plan.handle, self.y, self.z, self.sh)
+        pb = croft.croft_plan_pass_times(self.plan.handle)
+        stream.synchronize()
+        self.rec_pp.append((pf, pb))
+
+    def per_pass(self, steps):
+        self.croft.croft_plan_set_timing(self.plan.handle, True)
+        for _ in range(steps):
+            self.step_per_pass()
+        self.croft.croft_plan_set_timing(self.plan.handle, False)
+        npass = len(self.rec_pp[0][0])
+        return [statistics.mean([r[0][i] for r in self.rec_pp] + [r[1][i] for r in self.rec_pp]) for i in range(npass)]
+
+
+def run_croft(args):  # noqa: PLR0915
     import numpy as np
     import torch
 
@@ -532,7 +673,9 @@ def run_croft(args):
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
 
-    x_h = S.config_input("pme256")
+    t_in = time.perf_counter()
+    x_h = S.config_input(CONFIG)
+    t_in = time.perf_counter() - t_in
     shape = x_h.shape
     n_total = math.prod(shape)
     flops_step = 2 * nominal_flops(shape)
@@ -546,43 +689,17 @@ def run_croft(args):
     sched = {"auto": None, "three_pass": croft.CROFT_SCHEDULE_THREE_PASS,
              "plane_fused": croft.CROFT_SCHEDULE_PLANE_FUSED, "slab_l2": croft.CROFT_SCHEDULE_SLAB_L2}[args.schedule]
     plan = croft.Plan(*shape, schedule=sched)
-    plan_desc = plan.describe()
-    launches_per_step = 2 * croft.croft_plan_num_launches(plan.handle)
-    sh = stream.cuda_stream
+    plan_tc = None if args.no_tc else croft.Plan(*shape, dtype=croft.CROFT_C2C_F32_TC_BF16X3)
+    arms = {"fp32": Arm(croft, torch, stream, flush, plan, x, y, z)}
+    if plan_tc is not None:
+        arms["tc"] = Arm(croft, torch, stream, flush, plan_tc, x, y, z)
 
-    gap_fills = [1]
-
-    def step(record):
-        """One forward + backward; device time between two events (none between the passes)."""
-        with torch.cuda.stream(stream):
-            for _ in range(gap_fills[0]):
-                flush.fill_(1.0)
-            e = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
-            e[0].record(stream)
-            croft.croft_exec_forward(plan.handle, x, y, sh)
-            croft.croft_exec_backward(plan.handle, y, z, sh)
-            e[1].record(stream)
-        stream.synchronize()
-        if record is not None:
-            record.append(e[0].elapsed_time(e[1]))
-
-    def step_per_pass(record):
-        """The same step with an event after every pass (per-kernel durations)."""
-        with torch.cuda.stream(stream):
-            flush.fill_(1.0)
-            croft.croft_exec_forward(plan.handle, x, y, sh)
-        pf = croft.croft_plan_pass_times(plan.handle)
-        with torch.cuda.stream(stream):
-            croft.croft_exec_backward(plan.handle, y, z, sh)
-        pb = croft.croft_plan_pass_times(plan.handle)
-        stream.synchronize()
-        record.append((pf, pb))
-
-    for _ in range(args.warmup):
-        step(None)
+    for arm in arms.values():
+        for _ in range(args.warmup):
+            arm.step(None)
     # Untimed L2-flush writes between timed steps keep the GPU busy so that the
-    # timed region spans >= ~2 s of wall time: long enough for the clock samples
-    # to describe it, without idle gaps that would let the clocks drop.
+    # timed region spans >= ~2 s of wall time per path: long enough for the clock
+    # samples to describe it, without idle gaps that would let the clocks drop.
     with torch.cuda.stream(stream):
         a = torch.cuda.Event(enable_timing=True)
         b = torch.cuda.Event(enable_timing=True)
@@ -592,128 +709,148 @@ def run_croft(args):
         b.record(stream)
     stream.synchronize()
     t_fill = a.elapsed_time(b) / 10 * 1e-3
-    gap_fills[0] = max(1, int(math.ceil(args.clock_window_s / max(1, args.steps) / t_fill)))
-    if world > 1:
-        torch.distributed.barrier()
-    torch.cuda.synchronize()
+    fills = max(1, int(math.ceil(args.clock_window_s / max(1, args.steps) / t_fill)))
     clocks = ClockSampler(torch.cuda.current_device())
     clocks.start()
-    rec = []
-    t_wall = time.perf_counter()
-    for _ in range(args.steps):
-        step(rec)
-    torch.cuda.synchronize()
-    t_wall = time.perf_counter() - t_wall
+    t_wall = {}
+    for name, arm in arms.items():
+        if world > 1:
+            torch.distributed.barrier()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for _ in range(args.steps):
+            arm.step(arm.rec, fills)
+        torch.cuda.synchronize()
+        t_wall[name] = time.perf_counter() - t0
     # per-kernel durations: the same steps again with per-pass events, right after the timed ones
-    croft.croft_plan_set_timing(plan.handle, True)
-    rec_pp = []
-    for _ in range(args.steps):
-        step_per_pass(rec_pp)
-    croft.croft_plan_set_timing(plan.handle, False)
+    pass_ms = {name: arm.per_pass(args.steps) for name, arm in arms.items()}
     clk = clocks.stop()
-    ms_total = max_over_ranks(torch, sum(rec), dev)
-    ms_step = ms_total / args.steps
-    value = job_gflops(world, flops_step, ms_step)
-
-    # per-pass kernel times (forward and backward run the same kernels)
-    npass = len(rec_pp[0][0])
-    pass_ms = [statistics.mean([r[0][i] for r in rec_pp] + [r[1][i] for r in rec_pp]) for i in range(npass)]
-    dom = max(range(npass), key=lambda i: pass_ms[i])
-    axis_names = {3: ["z", "y", "x"], 2: ["yz", "x"], 1: ["yz"]}.get(npass, [f"p{i}" for i in range(npass)])
     peak, peak_kind = measured_peaks()
-    alg_bytes = 16.0 * n_total  # one read + one write of the grid per pass launch
-    # The per-pass events give each pass's share of a transform; an event between two
-    # passes also adds a gap and stops the next pass from launching early, so the sum of
-    # the per-pass times exceeds the timed step.  The dominant pass's duration inside the
-    # timed steps = its share x the timed time of one transform.
-    achieved_events = alg_bytes / (pass_ms[dom] * 1e-3) / 1e9
-    dom_ms_in_step = pass_ms[dom] / sum(pass_ms) * (ms_step / 2)
-    achieved = alg_bytes / (dom_ms_in_step * 1e-3) / 1e9
-    dom_key = f"pass_{axis_names[dom]}_{'x'.join(map(str, shape))}"
-    traffic = ncu_traffic(dom_key)
+    res = {}
+    for name, arm in arms.items():
+        ms_total = max_over_ranks(torch, sum(arm.rec), dev)
+        ms_step = ms_total / args.steps
+        src = TC_KERNEL_SOURCES if name == "tc" else PASS_KERNEL_SOURCES
+        res[name] = {"ms_per_step": ms_step, "value": job_gflops(world, flops_step, ms_step),
+                     "roofline": roofline(pass_ms[name], ms_step, shape, peak, peak_kind,
+                                          "_tc" if name == "tc" else "", src),
+                     "hbm_frac_whole_transform": (16.0 * n_total * 2 / (ms_step * 1e-3) / 1e9) / peak,
+                     "plan": arm.plan.describe(),
+                     "launches_per_step": 2 * croft.croft_plan_num_launches(arm.plan.handle)}
+    ms_step = res["fp32"]["ms_per_step"]
+    value = res["fp32"]["value"]
+
+    # errors against the FP64 oracle on the full grid, for every path (outside the timed regions)
+    errors = None
+    if rank == 0 and not args.no_errors:
+        import oracle
+        t0 = time.perf_counter()
+        ref = oracle.forward(x_h)
+        t_oracle = time.perf_counter() - t0
+        errors = {"oracle": f"oracle.forward (FP64 per-axis DFT matrices) on the same complex64 input, "
+                            f"{t_oracle:.1f} s on {os.cpu_count()} host cores"}
+        for name, arm in arms.items():
+            with torch.cuda.stream(stream):
+                croft.croft_exec_forward(arm.plan.handle, x, y, stream.cuda_stream)
+                croft.croft_exec_backward(arm.plan.handle, y, z, stream.cuda_stream)
+            stream.synchronize()
+            st = croft.croft_plan_last_device_status(arm.plan.handle)
+            e = errors_vs_oracle(x_h, y.cpu().numpy(), z.cpu().numpy(), ref)
+            bar = TC_TOL if name == "tc" else FP32_TOL_PER_LOG2 * math.log2(n_total)
+            e.update({"bar_rel_l2": bar, "within_bar": e["rel_l2_fwd"] <= bar and e["rel_l2_roundtrip"] <= bar,
+                      "device_status": croft.croft_status_string(st)})
+            errors[name] = e
+        del ref
+    if "tc" in res:
+        res["tc"]["tc_vs_fp32"] = {"time_ratio": res["tc"]["ms_per_step"] / ms_step,
+                                   "gflops_ratio": res["tc"]["value"] / value}
+        if errors:
+            res["tc"]["errors"] = errors["tc"]
+            res["tc"]["tc_vs_fp32"]["rel_l2_fwd_ratio"] = errors["tc"]["rel_l2_fwd"] / errors["fp32"]["rel_l2_fwd"]
 
     # end to end through the C ABI with host buffers: every step uploads its input grid from
     # pinned memory, runs forward + backward and downloads the result; the library's host
     # pipeline overlaps the copies of one step with the transforms of its neighbours.
-    x_pin = torch.from_numpy(x_h).pin_memory()
-    z_pin = torch.empty_like(x_pin).pin_memory()
-    ops = croft.CROFT_OP_FORWARD | croft.CROFT_OP_BACKWARD
-    croft.croft_exec_host_pipeline(plan.handle, [x_pin] * args.warmup, [z_pin] * args.warmup, ops, stream)
-    stream.synchronize()
-    with torch.cuda.stream(stream):
-        flush.fill_(1.0)
-        a = torch.cuda.Event(enable_timing=True)
-        b = torch.cuda.Event(enable_timing=True)
-        a.record(stream)
-        croft.croft_exec_host_pipeline(plan.handle, [x_pin] * args.steps, [z_pin] * args.steps, ops, stream)
-        b.record(stream)
-    stream.synchronize()
-    e2e_ms = a.elapsed_time(b) / args.steps
-    # the same with each step's copies and transforms serialised on one stream, for reference
-    e2e_serial = []
-    for i in range(args.warmup + args.steps):
+    e2e = None
+    if not args.no_e2e:
+        x_pin = torch.from_numpy(x_h).pin_memory()
+        z_pin = torch.empty_like(x_pin).pin_memory()
+        ops = croft.CROFT_OP_FORWARD | croft.CROFT_OP_BACKWARD
+        croft.croft_exec_host_pipeline(plan.handle, [x_pin] * args.warmup, [z_pin] * args.warmup, ops, stream)
+        stream.synchronize()
         with torch.cuda.stream(stream):
             flush.fill_(1.0)
             a = torch.cuda.Event(enable_timing=True)
             b = torch.cuda.Event(enable_timing=True)
             a.record(stream)
-            x.copy_(x_pin, non_blocking=True)
-            croft.croft_exec_forward(plan.handle, x, y, sh)
-            croft.croft_exec_backward(plan.handle, y, z, sh)
-            z_pin.copy_(z, non_blocking=True)
+            croft.croft_exec_host_pipeline(plan.handle, [x_pin] * args.steps, [z_pin] * args.steps, ops, stream)
             b.record(stream)
         stream.synchronize()
-        if i >= args.warmup:
-            e2e_serial.append(a.elapsed_time(b))
-    e2e_serial_ms = statistics.mean(e2e_serial)
-    # the host link's own rate for this traffic: one step's upload and download at once, on two
-    # streams, copy engines only (the pipelined e2e step cannot beat it)
-    s2 = torch.cuda.Stream(device=dev)
-    link = []
-    for i in range(5):
-        with torch.cuda.stream(stream):
-            a = torch.cuda.Event(enable_timing=True)
-            b = torch.cuda.Event(enable_timing=True)
-            a.record(stream)
-            s2.wait_event(a)
-            x.copy_(x_pin, non_blocking=True)
-        with torch.cuda.stream(s2):
-            z_pin.copy_(z, non_blocking=True)
-            c = torch.cuda.Event()
-            c.record(s2)
-        with torch.cuda.stream(stream):
-            stream.wait_event(c)
-            b.record(stream)
-        stream.synchronize()
-        if i >= 1:
-            link.append(a.elapsed_time(b))
-    link_ms = statistics.median(link)
-    link_gbs = 16.0 * n_total / (link_ms * 1e-3) / 1e9
-    e2e_ms = max_over_ranks(torch, e2e_ms, dev)
-    e2e_val = job_gflops(world, flops_step, e2e_ms)
-    zr = z_pin.numpy().astype(np.complex128)
-    xr = x_h.astype(np.complex128) * n_total
-    e2e_check = float(np.linalg.norm(zr - xr) / np.linalg.norm(xr))
+        e2e_ms = a.elapsed_time(b) / args.steps
+        # the round trip the pipelined steps brought back (before z_pin is reused below)
+        zr = z_pin.numpy()
+        num = den = 0.0
+        for x0 in range(0, shape[0], 64):
+            xr = x_h[x0:x0 + 64].astype(np.complex128) * n_total
+            d = zr[x0:x0 + 64].astype(np.complex128) - xr
+            num += float((d.real ** 2 + d.imag ** 2).sum())
+            den += float((xr.real ** 2 + xr.imag ** 2).sum())
+        # the host link's own rate for this traffic: one step's upload and download at once, on two
+        # streams, copy engines only (the pipelined e2e step cannot beat it)
+        s2 = torch.cuda.Stream(device=dev)
+        link = []
+        for i in range(5):
+            with torch.cuda.stream(stream):
+                a = torch.cuda.Event(enable_timing=True)
+                b = torch.cuda.Event(enable_timing=True)
+                a.record(stream)
+                s2.wait_event(a)
+                x.copy_(x_pin, non_blocking=True)
+            with torch.cuda.stream(s2):
+                z_pin.copy_(z, non_blocking=True)
+                c = torch.cuda.Event()
+                c.record(s2)
+            with torch.cuda.stream(stream):
+                stream.wait_event(c)
+                b.record(stream)
+            stream.synchronize()
+            if i >= 1:
+                link.append(a.elapsed_time(b))
+        link_ms = statistics.median(link)
+        link_gbs = 16.0 * n_total / (link_ms * 1e-3) / 1e9
+        e2e_ms = max_over_ranks(torch, e2e_ms, dev)
+        e2e = {"value": job_gflops(world, flops_step, e2e_ms), "unit": "GFLOP/s", "h2d_bytes_per_step": 8 * n_total,
+               "d2h_bytes_per_step": 8 * n_total, "ms_per_step": e2e_ms,
+               "api": "croft_exec_host_pipeline (upload, forward, backward, download per step; "
+                      "steps overlapped on three streams), FP32 path",
+               "roundtrip_rel_l2": math.sqrt(num / den),
+               "link_roofline": {"bound": "host link", "achieved_gbs": 16.0 * n_total / (e2e_ms * 1e-3) / 1e9,
+                                 "peak_gbs": link_gbs, "frac": link_ms / e2e_ms,
+                                 "peak_source": "this step's upload and download copied at once on two "
+                                                "streams, measured here"}}
+        del x_pin, z_pin
 
     rows = None
     if rank == 0 and not args.no_rows:
         only = None if args.rows == "all" else set(args.rows.split(","))
-        rows = measure_rows(croft, torch, dev, stream, flush, peak, only)
+        rows = measure_rows(croft, torch, dev, stream, flush, peak, peak_kind, only)
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        # whole forward+backward steps of the oracle, repeated for >= 10 s (at most 30 s)
+        # the oracle on a bounded sample of the same workload: a fraction of the pencils of every
+        # axis per forward+backward step, repeated for >= 10 s
+        sample = oracle_sample_planes(x_h, 3.0)
         t0 = time.perf_counter()
         fl, reps = 0.0, 0
         while True:
-            fl += cpu_oracle_step(x_h, None)
+            fl += cpu_oracle_step(x_h, sample)
             reps += 1
             dt = time.perf_counter() - t0
             if dt >= 10.0 or dt * (reps + 1) / reps > 30.0:
                 break
         cpu = {"value": fl / dt / 1e9, "unit": "GFLOP/s", "cores": os.cpu_count(), "kind": "oracle",
-               "sample": f"FP64 oracle (numpy matmul per-axis DFT), {reps} full forward+backward step(s) of the "
-                         f"pme256 grid in {dt:.1f} s"}
+               "sample": f"FP64 oracle (numpy matmul per-axis DFT): {reps} forward+backward step(s) on {sample}/"
+                         f"{shape[0]} of the pencils of each axis of the {CONFIG} grid, {dt:.1f} s"}
 
     # library context (not targets, not oracles): cuFFT through torch.fft on the same grid and
     # protocol, and a multi-threaded CPU FFT (scipy's pocketfft) on the host cores
@@ -721,46 +858,31 @@ def run_croft(args):
     if rank == 0 and not args.no_rows:
         context = library_context(torch, x, flush, stream, x_h, flops_step, args.no_cpu_baseline)
 
+    launches = sum(r["launches_per_step"] for r in res.values()) * args.steps
     plan.close()
+    if plan_tc is not None:
+        plan_tc.close()
     if rank == 0:
+        fp = res["fp32"]
         line = {
             "metric": METRIC, "value": value, "unit": "GFLOP/s", "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f32", "data": "synthetic",
             "config": {"workload": WORKLOAD, "grid": list(shape), "direction": "forward+backward",
-                       "l2": "flushed before every step (writes of a 1 GiB buffer, > 2x L2, outside the timed events)",
+                       "l2": "inputs (1 GiB) larger than L2; L2 also flushed before every step (writes of a "
+                             "1 GiB buffer, outside the timed events)",
                        "parallelism": f"replicas x{world}" if world > 1 else "single GPU",
-                       "passes_per_direction": npass, "schedule": args.schedule, "plan": plan_desc},
-            "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
-                         "frac": achieved / peak, "traffic": traffic, "kernel": dom_key,
-                         "kernel_source_sha": kernel_source_sha(),
-                         "peak_source": peak_kind, "alg_bytes_per_launch": alg_bytes,
-                         "pass_ms": pass_ms, "dominant_ms_in_timed_step": dom_ms_in_step,
-                         "achieved_per_pass_events": achieved_events,
-                         "frac_per_pass_events": achieved_events / peak,
-                         "kernel_timing": "per-pass shares from CUDA events on the launch stream after "
-                                          f"every pass, over {args.steps} forward+backward steps run right "
-                                          "after the timed ones; absolute duration = share x the timed "
-                                          "time of one transform (an event between two passes adds a gap "
-                                          "and stops the next pass from launching early, so the timed "
-                                          "steps carry events only at their ends; achieved_per_pass_events "
-                                          "is the same figure from the per-pass events alone)"},
-            "hbm_frac_whole_transform": (16.0 * n_total * 2 / (ms_step * 1e-3) / 1e9) / peak,
+                       "passes_per_direction": len(pass_ms["fp32"]), "schedule": args.schedule,
+                       "plan": fp["plan"], "input_generation_s": t_in},
+            "roofline": fp["roofline"],
+            "hbm_frac_whole_transform": fp["hbm_frac_whole_transform"],
+            "errors": errors,
+            "tc": res.get("tc"),
             "cpu_baseline": cpu,
             "library_context": context,
-            "e2e": {"value": e2e_val, "unit": "GFLOP/s", "h2d_bytes_per_step": 8 * n_total,
-                    "d2h_bytes_per_step": 8 * n_total, "ms_per_step": e2e_ms,
-                    "api": "croft_exec_host_pipeline (upload, forward, backward, download per step; "
-                           "steps overlapped on three streams)",
-                    "roundtrip_rel_l2": e2e_check,
-                    "serialised_ms_per_step": e2e_serial_ms,
-                    "serialised_value": job_gflops(world, flops_step, e2e_serial_ms),
-                    "link_roofline": {"bound": "host link", "achieved_gbs": 16.0 * n_total / (e2e_ms * 1e-3) / 1e9,
-                                      "peak_gbs": link_gbs, "frac": link_ms / e2e_ms,
-                                      "peak_source": "this step's upload and download copied at once on two "
-                                                     "streams, measured here"}},
-            "gpu_launches": launches_per_step * args.steps,
-            "gpu_launches_note": "croft kernels inside the device-timed steps (the e2e region launches the same per step)",
+            "e2e": e2e,
+            "gpu_launches": launches,
+            "gpu_launches_note": "croft kernels inside the device-timed steps of both paths",
             "rows": rows,
             "clocks": clk,
             "wall_s_timed_region": t_wall,
@@ -778,12 +900,17 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="croft", choices=["croft", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-errors", action="store_true", help="skip the oracle comparison of the headline results")
+    ap.add_argument("--no-e2e", action="store_true", help="skip the end-to-end (host buffers) measurement")
+    ap.add_argument("--no-tc", action="store_true", help="time the FP32 path only")
+    ap.add_argument("--reference-budget-s", type=float, default=180.0,
+                    help="--impl reference: wall time of all its (warm-up + timed) oracle steps")
     ap.add_argument("--schedule", default="auto", choices=["auto", "three_pass", "plane_fused", "slab_l2"])
     ap.add_argument("--no-rows", action="store_true", help="skip the extra per-row measurements")
     ap.add_argument("--rows", default="all",
                     help="comma-separated subset of the extra rows (" + ", ".join(ROW_NAMES) + ") or 'all'")
     ap.add_argument("--clock-window-s", type=float, default=2.0,
-                    help="minimum wall time of the timed region, padded with untimed L2-flush writes "
+                    help="minimum wall time of each timed region, padded with untimed L2-flush writes "
                          "between steps (0 under a profiler)")
     args = ap.parse_args()
     if args.warmup < 3:

@@ -45,11 +45,20 @@ typedef enum {
     CROFT_C2C_F32 = 0,           /* complex64 in/out, FP32 CUDA-core butterflies */
     CROFT_C2C_F32_TC_BF16X3 = 1, /* complex64 in/out, radix-16 stages on tensor cores
                                     (split bf16 hi+lo operands, FP32 accumulate) */
-    CROFT_C2C_F64 = 2            /* complex128 in/out (16-byte elements), FP64 butterflies and
+    CROFT_C2C_F64 = 2,           /* complex128 in/out (16-byte elements), FP64 butterflies and
                                     twiddles: the paper's double complex (Sec. 5).  Axes: powers of
                                     two up to 1024 and 3, 5, 6, 10, 12, 15, 48, 60, 96, 120; three-pass
                                     schedule; single-grid plans only */
+    CROFT_C2C_F32_TC_FP16X3 = 3  /* complex64 in/out, radix-16 stages on tensor cores with split
+                                    fp16 hi+lo operands (~22 significant bits), each butterfly
+                                    scaled by a power of two into fp16's range first, FP32
+                                    accumulate */
 } croft_dtype;
+/* Tensor-core dtypes (CROFT_C2C_F32_TC_*): every axis whose length has a factor 16 runs its
+ * radix-16 stages as split-operand GEMMs on the tensor cores (axes of 16 .. 1024 points; a
+ * longer one makes plan creation fail with CROFT_ERR_UNSUPPORTED_SIZE rather than fall back
+ * to FP32); an axis without a factor 16 has no radix-16 stage and runs on the CUDA cores.
+ * croft_plan_tc_axes reports which axes run on the tensor cores. */
 
 typedef enum {
     CROFT_OK = 0,
@@ -76,7 +85,8 @@ const char* croft_status_string(croft_status s);
  *   out   : receives the plan (set to NULL on failure).
  *   nx,ny,nz : axis lengths, each 1..4096 and 2^a 3^b 5^c.  A length-1 axis
  *           is the identity.
- *   dtype : CROFT_C2C_F32, CROFT_C2C_F32_TC_BF16X3 or CROFT_C2C_F64.
+ *   dtype : CROFT_C2C_F32, CROFT_C2C_F32_TC_BF16X3, CROFT_C2C_F32_TC_FP16X3 or
+ *           CROFT_C2C_F64.
  * Returns CROFT_OK, CROFT_ERR_INVALID_ARG (out NULL, bad dtype),
  * CROFT_ERR_UNSUPPORTED_SIZE, CROFT_ERR_OOM or CROFT_ERR_CUDA.
  * The environment variable CROFT_LOG=1 prints the chosen schedule to stderr.
@@ -108,6 +118,14 @@ typedef enum {
     CROFT_SCHEDULE_PLANE_FUSED = 2,
     CROFT_SCHEDULE_SLAB_L2 = 3
 } croft_schedule;
+
+/*
+ * croft_plan_tc_axes - which axes of a single-grid plan run their radix-16 stages on the
+ * tensor cores: bit a set for axis a (0 = x, 1 = y, 2 = z).  0 for FP32 / FP64 plans, batched
+ * plans and NULL.  The library's own statement of a plan's per-axis arithmetic (the
+ * precision of every result of a tensor-core plan follows from it).
+ */
+int croft_plan_tc_axes(croft_plan plan);
 
 /* croft_plan_create with an explicit schedule (same arguments and errors;
  * CROFT_ERR_INVALID_ARG for an unknown schedule). */
@@ -209,7 +227,14 @@ croft_status croft_plan_set_test_unsatisfiable_wait(croft_plan plan, int enable)
  * the host, copies them into the array on `stream`, clears the counters and
  * launches; it calls no cudaMalloc / cudaFree and no allocating library
  * routine.  The first call on a device looks up the array's device address
- * (cudaGetSymbolAddress); make that first call before any stream capture.
+ * (cudaGetSymbolAddress) and keeps it for the life of the process; make that
+ * first call before any stream capture, and do not use the entry point across
+ * a cudaDeviceReset (the kept address would belong to the destroyed context).
+ * The tables are copied from host memory that the call owns only while it
+ * runs (pageable; cudaMemcpyAsync stages it before returning), so a copy
+ * recorded into a graph would read freed memory when replayed: the call
+ * returns CROFT_ERR_INVALID_ARG, before any device work, when `stream` is
+ * capturing.
  *
  *   count     : number of grids, 1..CROFT_NOALLOC_MAX_GRIDS.
  *   dims      : host array of 3*count axis lengths; each axis 1..128 of the
@@ -219,7 +244,9 @@ croft_status croft_plan_set_test_unsatisfiable_wait(croft_plan plan, int enable)
  *               or disjoint).
  *   direction : -1 forward (Eq. 1), +1 backward (Eq. 2, unnormalised).
  *   stream    : cudaStream_t or NULL.
- * Returns CROFT_OK, CROFT_ERR_INVALID_ARG, CROFT_ERR_UNSUPPORTED_SIZE (more
+ * Returns CROFT_OK, CROFT_ERR_INVALID_ARG (NULL or misaligned pointers, a
+ * direction other than -1 / +1, partial overlap of in[g] and out[g], or a
+ * capturing stream), CROFT_ERR_UNSUPPORTED_SIZE (more
  * than CROFT_NOALLOC_MAX_GRIDS grids, an axis outside the list above, or more
  * than CROFT_NOALLOC_MAX_ITEMS work items - a 128^3 grid has 1536 - i.e. the
  * batch does not fit the static array) or CROFT_ERR_CUDA.
@@ -248,6 +275,35 @@ croft_status croft_exec_batched_noalloc(int count, const int* dims, void* const*
  */
 croft_status croft_exec_forward(croft_plan plan, const void* in, void* out, void* stream);
 croft_status croft_exec_backward(croft_plan plan, const void* in, void* out, void* stream);
+
+/*
+ * croft_exec_axes - the 1D transforms of a subset of the axes only (Eq. 1 / Eq. 2 restricted
+ * to those axes; the others untouched): the local steps of a transform whose grid is
+ * distributed over several processes or GPUs in slabs (Sec. 2.2.1, and steps 1, 5 and 9 of
+ * Sec. 4.1).  A process holding an x-slab runs the z and y axes, an all-to-all regroups the
+ * grid into y-slabs, and each process then runs the x axis.
+ *
+ *   plan      : a single-grid plan with one pass per axis (CROFT_SCHEDULE_THREE_PASS, which
+ *               AUTO gives); the fused-plane and slab schedules give CROFT_ERR_INVALID_ARG.
+ *   in, out   : device pointers as for croft_exec_forward (in == out allowed).
+ *   axes      : bit a set to transform axis a (0 = x, 1 = y, 2 = z); 0 copies in to out.
+ *   direction : -1 forward (Eq. 1), +1 backward (Eq. 2, unnormalised).
+ *   stream    : cudaStream_t or NULL.
+ * Returns CROFT_OK, CROFT_ERR_INVALID_ARG or CROFT_ERR_CUDA.  Asynchronous like exec.
+ */
+croft_status croft_exec_axes(croft_plan plan, const void* in, void* out, int axes, int direction, void* stream);
+
+/*
+ * croft_transpose_blocks - out[j][i] = in[i][j] for an in array of d0 x d1 blocks of
+ * block_bytes each (C order): the pack / unpack of the slab exchange (the paper's pack and
+ * unpack around the all-to-all, Sec. 4.1 steps 2 and 4), as pitched copy-engine copies on
+ * `stream` (min(d0, d1) of them).  No library allocation.
+ *
+ *   in, out : device pointers, disjoint (overlap gives CROFT_ERR_INVALID_ARG).
+ * Returns CROFT_OK, CROFT_ERR_INVALID_ARG or CROFT_ERR_CUDA.
+ */
+croft_status croft_transpose_blocks(const void* in, void* out, long long d0, long long d1, long long block_bytes,
+                                    void* stream);
 
 /*
  * croft_exec_convolve - the reciprocal-space step of particle-mesh Ewald, the

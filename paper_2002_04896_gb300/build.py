@@ -42,14 +42,14 @@ def _units():
     for g in range(N_GROUPS):
         units.append((os.path.join(CSRC, "croft_kernels.cu"), os.path.join(BUILD, f"croft_kernels_g{g}.o"),
                       [f"-DCROFT_GROUP={g}"]))
-    for g in range(2):
-        units.append((os.path.join(CSRC, "croft_pipe.cu"), os.path.join(BUILD, f"croft_pipe_g{g}.o"),
-                      [f"-DCROFT_PIPE_GROUP={g}"]))
     for g in range(5):
         units.append((os.path.join(CSRC, "croft_conv.cu"), os.path.join(BUILD, f"croft_conv_g{g}.o"),
                       [f"-DCROFT_CONV_GROUP={g}"]))
+    for g in range(4):
+        units.append((os.path.join(CSRC, "croft_tc.cu"), os.path.join(BUILD, f"croft_tc_g{g}.o"),
+                      [f"-DCROFT_TC_GROUP={g}"]))
     for src in sorted(glob.glob(os.path.join(CSRC, "*.cu"))):
-        if os.path.basename(src) in ("croft_kernels.cu", "croft_pipe.cu", "croft_conv.cu"):
+        if os.path.basename(src) in ("croft_kernels.cu", "croft_conv.cu"):
             continue
         obj = os.path.join(BUILD, os.path.basename(src)[:-3] + ".o")
         units.append((src, obj, []))

@@ -20,6 +20,7 @@ _lib = ctypes.CDLL(_LIB_PATH)
 CROFT_C2C_F32 = 0
 CROFT_C2C_F32_TC_BF16X3 = 1
 CROFT_C2C_F64 = 2
+CROFT_C2C_F32_TC_FP16X3 = 3
 
 CROFT_SCHEDULE_AUTO = 0
 CROFT_SCHEDULE_THREE_PASS = 1
@@ -83,6 +84,10 @@ _debug_live_allocations = _sig("croft_debug_live_allocations", ctypes.c_long, []
 _exec_batched_noalloc = _sig("croft_exec_batched_noalloc", _I,
                              [_I, ctypes.POINTER(_I), ctypes.POINTER(_P), ctypes.POINTER(_P), _I, _P])
 _exec_convolve = _sig("croft_exec_convolve", _I, [_P, _P, _P, _P, _P])
+_tc_axes = _sig("croft_plan_tc_axes", _I, [_P])
+_exec_axes = _sig("croft_exec_axes", _I, [_P, _P, _P, _I, _I, _P])
+_transpose_blocks = _sig("croft_transpose_blocks", _I,
+                         [_P, _P, ctypes.c_longlong, ctypes.c_longlong, ctypes.c_longlong, _P])
 _twiddle_table = _sig("croft_twiddle_table", _I, [_I, ctypes.POINTER(_I), _I, ctypes.POINTER(ctypes.c_float)])
 
 LIBRARY_PATH = _LIB_PATH
@@ -93,7 +98,8 @@ EXPORTED = [
     "croft_twiddle_table", "croft_plan_create_batched", "croft_plan_create_batched_mode",
     "croft_exec_batched_forward", "croft_exec_batched_backward", "croft_plan_set_wait_limit",
     "croft_plan_set_test_unsatisfiable_wait", "croft_exec_batched_noalloc", "croft_debug_fail_allocation",
-    "croft_debug_live_allocations", "croft_exec_host_pipeline", "croft_exec_convolve",
+    "croft_debug_live_allocations", "croft_exec_host_pipeline", "croft_exec_convolve", "croft_plan_tc_axes",
+    "croft_exec_axes", "croft_transpose_blocks",
 ]
 
 
@@ -124,6 +130,21 @@ def _stream_ptr(stream) -> int:
     return int(stream.cuda_stream)
 
 
+def _check_layout(x, numel=None, complex128=None) -> None:
+    """dtype, contiguity and element count of a tensor argument (no device check)."""
+    import torch
+    if not isinstance(x, torch.Tensor):
+        raise TypeError("expected a torch CUDA tensor or an integer device address")
+    allowed = ((torch.complex64, torch.complex128) if complex128 is None
+               else ((torch.complex128,) if complex128 else (torch.complex64,)))
+    if x.dtype not in allowed:
+        raise ValueError(f"croft: expected {' or '.join(map(str, allowed))}, got {x.dtype}")
+    if not x.is_contiguous():
+        raise ValueError("croft: tensors must be C-contiguous in (nx, ny, nz) order")
+    if numel is not None and x.numel() != numel:
+        raise ValueError(f"croft: tensor has {x.numel()} elements, plan expects {numel}")
+
+
 def _ptr(x, numel=None, complex128=None) -> int:
     """Device address of a raw pointer (int) or of a C-contiguous complex CUDA tensor.
 
@@ -135,18 +156,9 @@ def _ptr(x, numel=None, complex128=None) -> int:
     if isinstance(x, int):
         return x
     import torch
-    if not isinstance(x, torch.Tensor):
-        raise TypeError("expected a torch CUDA tensor or an integer device address")
+    _check_layout(x, numel, complex128)
     if not x.is_cuda:
         raise ValueError("croft: tensors must live on a CUDA device")
-    allowed = ((torch.complex64, torch.complex128) if complex128 is None
-               else ((torch.complex128,) if complex128 else (torch.complex64,)))
-    if x.dtype not in allowed:
-        raise ValueError(f"croft: expected {' or '.join(map(str, allowed))}, got {x.dtype}")
-    if not x.is_contiguous():
-        raise ValueError("croft: tensors must be C-contiguous in (nx, ny, nz) order")
-    if numel is not None and x.numel() != numel:
-        raise ValueError(f"croft: tensor has {x.numel()} elements, plan expects {numel}")
     return int(x.data_ptr())
 
 
@@ -221,6 +233,35 @@ def croft_exec_backward(plan: int, inp, out, stream=None) -> None:
 def croft_exec_convolve(plan: int, inp, out, g, stream=None) -> None:
     """out = B(G * F(in)): the PME reciprocal-space convolution (see include/croft.h)."""
     _check(croft_exec_convolve_status(plan, inp, out, g, stream), "croft_exec_convolve")
+
+
+def croft_exec_axes_status(plan: int, inp, out, axes: int, direction: int, stream=None) -> int:
+    return _exec_axes(plan, _ptr(inp), _ptr(out), int(axes), int(direction), _stream_ptr(stream))
+
+
+def croft_exec_axes(plan: int, inp, out, axes: int, direction: int, stream=None) -> None:
+    """The 1D transforms of the axes in the bit mask `axes` (bit a: axis a; 0 = x): direction -1
+    forward (Eq. 1), +1 backward (Eq. 2)."""
+    _check(croft_exec_axes_status(plan, inp, out, axes, direction, stream), "croft_exec_axes")
+
+
+def croft_transpose_blocks(inp, out, d0: int, d1: int, block_bytes: int, stream=None) -> None:
+    """out[j][i] = in[i][j] over d0 x d1 blocks of block_bytes (device tensors or addresses)."""
+    def addr(t):
+        if isinstance(t, int):
+            return t
+        if not t.is_cuda or not t.is_contiguous():
+            raise ValueError("croft: contiguous CUDA tensors expected")
+        if t.numel() * t.element_size() < d0 * d1 * block_bytes:
+            raise ValueError("croft: tensor smaller than d0 * d1 * block_bytes")
+        return int(t.data_ptr())
+    _check(_transpose_blocks(addr(inp), addr(out), int(d0), int(d1), int(block_bytes), _stream_ptr(stream)),
+           "croft_transpose_blocks")
+
+
+def croft_plan_tc_axes(plan: int) -> int:
+    """Bit a set when axis a (0 = x, 1 = y, 2 = z) runs its radix-16 stages on the tensor cores."""
+    return int(_tc_axes(plan))
 
 
 def croft_plan_workspace_bytes(plan: int) -> int:
@@ -325,11 +366,27 @@ def croft_plan_set_test_unsatisfiable_wait(plan: int, enable: bool) -> None:
 
 
 def croft_exec_batched_noalloc_status(dims, ins, outs, direction: int, stream=None) -> int:
-    """The allocation-free batched entry point: direction -1 forward (Eq. 1), +1 backward (Eq. 2)."""
-    flat = [int(v) for d in dims for v in d]
+    """The allocation-free batched entry point: direction -1 forward (Eq. 1), +1 backward (Eq. 2).
+
+    The C side trusts `dims` for every size, so the lists are checked here first: one
+    complex64 tensor (or raw address) in and out per grid, each with the grid's element count.
+    """
+    dims = [tuple(int(v) for v in d) for d in dims]
+    if any(len(d) != 3 for d in dims):
+        raise ValueError("croft: each grid needs three axis lengths")
+    if len(ins) != len(dims) or len(outs) != len(dims):
+        raise ValueError(f"croft: {len(dims)} grids need as many inputs and outputs "
+                         f"(got {len(ins)} and {len(outs)})")
+    sizes = [d[0] * d[1] * d[2] for d in dims]
+    for i, x in enumerate(list(ins) + list(outs)):
+        if not isinstance(x, int):
+            _check_layout(x, sizes[i % len(dims)], complex128=False)
+    pin = [_ptr(x, sizes[i], complex128=False) for i, x in enumerate(ins)]
+    pout = [_ptr(x, sizes[i], complex128=False) for i, x in enumerate(outs)]
+    flat = [v for d in dims for v in d]
     arr = (_I * max(1, len(flat)))(*flat)
-    return _exec_batched_noalloc(len(dims), arr, _ptr_array(ins), _ptr_array(outs), int(direction),
-                                 _stream_ptr(stream))
+    return _exec_batched_noalloc(len(dims), arr, (_P * max(1, len(pin)))(*pin), (_P * max(1, len(pout)))(*pout),
+                                 int(direction), _stream_ptr(stream))
 
 
 def croft_exec_batched_noalloc(dims, ins, outs, direction: int, stream=None) -> None:

@@ -44,7 +44,8 @@ static_assert(kNaGridsOff % 16 == 0 && kNaItemsOff % 16 == 0 && kNaTwOff % 16 ==
 static __device__ __align__(256) unsigned char g_noalloc_scratch[kNaBytes];
 
 // Device address of g_noalloc_scratch on the current device, looked up once per
-// device (host code may not use the symbol itself as a device pointer).
+// device and kept for the life of the process (host code may not use the symbol
+// itself as a device pointer; after a cudaDeviceReset the kept address is stale).
 static croft_status noalloc_scratch(unsigned char** out) {
     static std::mutex mu;
     static void* addr[64] = {nullptr};
@@ -74,6 +75,14 @@ using namespace croft;
 extern "C" croft_status croft_exec_batched_noalloc(int count, const int* dims, void* const* in, void* const* out,
                                                    int direction, void* stream) {
     if (count < 1 || !dims || !in || !out || (direction != 1 && direction != -1)) return CROFT_ERR_INVALID_ARG;
+    // The host tables below live only for this call: a copy captured into a graph would read
+    // freed memory on every replay, so a capturing stream is refused before any device work.
+    cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+    if (cudaStreamIsCapturing((cudaStream_t)stream, &cap) != cudaSuccess) {
+        cudaGetLastError();
+        return CROFT_ERR_INVALID_ARG;
+    }
+    if (cap != cudaStreamCaptureStatusNone) return CROFT_ERR_INVALID_ARG;
     if (count > kNaMaxGrids) return CROFT_ERR_UNSUPPORTED_SIZE;
     for (int i = 0; i < 3 * count; ++i)
         if (dims[i] != 1 && !batch_size_supported(dims[i])) return CROFT_ERR_UNSUPPORTED_SIZE;

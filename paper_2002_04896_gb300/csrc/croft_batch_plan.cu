@@ -13,7 +13,7 @@
 // ONE_LAUNCH, PER_PASS and GROUPED are recorded once into a CUDA graph per direction
 // (descriptor upload from pinned memory, counter reset, kernel launch(es));
 // an exec fills in the grids' pointers and launches the graph.  AUTO times the
-// three schedules on scratch buffers at plan creation and keeps the fastest,
+// four schedules on scratch buffers at plan creation and keeps the fastest,
 // caching the choice on disk (like FFTW wisdom) keyed by the batch's sizes, the
 // GPU name and the CUDA runtime version.
 //
@@ -491,7 +491,9 @@ croft_status croft_plan_create_batched_mode(croft_plan* out, int count, const in
     if (!out) return CROFT_ERR_INVALID_ARG;
     *out = NULL;
     if (count < 1 || !dims) return CROFT_ERR_INVALID_ARG;
-    if (dtype != CROFT_C2C_F32) return dtype == CROFT_C2C_F32_TC_BF16X3 ? CROFT_ERR_UNSUPPORTED_SIZE : CROFT_ERR_INVALID_ARG;
+    if (dtype != CROFT_C2C_F32)
+        return (dtype == CROFT_C2C_F32_TC_BF16X3 || dtype == CROFT_C2C_F32_TC_FP16X3) ? CROFT_ERR_UNSUPPORTED_SIZE
+                                                                                  : CROFT_ERR_INVALID_ARG;
     if (mode < CROFT_BATCH_AUTO || mode > CROFT_BATCH_GROUPED) return CROFT_ERR_INVALID_ARG;
     for (int i = 0; i < 3 * count; ++i)
         if (croft_make_sched(dims[i]).count < 0) return CROFT_ERR_UNSUPPORTED_SIZE;

@@ -43,20 +43,21 @@ typedef void (*pass64_fn)(const double2*, double2*, const PassArgs);
 typedef void (*conv_fn)(const float2*, float2*, const float*, const PassArgs);
 typedef void (*conv64_fn)(const double2*, double2*, const double*, const PassArgs);
 
-// TMA-pipelined persistent pass (croft_pipe_kernel.cuh).
-struct PipeArgs {
-    const float2* tw;          // twiddle table (N-1 entries)
-    long long M;               // COL: element stride of the axis (inner extent of the tensor map)
-    long long ncols;           // ROW: number of pencils
-    long long ntiles;
-    long long tiles_per_row;   // COL: ceil(M / W)
-    int W;                     // pencils per tile
-    int buf_elems;             // float2 slots per buffer (>= the padded ROW layout)
-    int tw_pad;
-    int box_rows;              // COL: rows per tensor-map box (divides N, <= 256)
-    float isign;
+constexpr int kRingTileWidth = 16;  // columns per tile of the ring column kernel (128-byte rows)
+
+// Column pass fed by tensor copies through a ring of tile buffers (croft_ring_kernel.cuh).
+struct RingArgs {
+    const float2* tw;          // twiddle table of the axis (N-1 entries, the column schedule)
+    long long M;               // element stride of the axis (inner extent of the tensor map)
+    long long ntiles;          // batch rows x tiles_per_row
+    long long tiles_per_row;   // ceil(M / 16)
+    long long wait_cycles;     // bound of every mbarrier wait (SM clocks)
+    int* status;               // device status word (CROFT_ERR_TIMEOUT), may be null
+    int box_rows;              // rows per tensor-map box (divides N, <= 256)
+    int tw_pad;                // float2 slots reserved for twiddles in shared memory
+    float isign;               // +1 forward, -1 backward (conj-in / conj-out)
 };
-typedef void (*pipe_fn)(const float2*, float2*, const PipeArgs, const CUtensorMap);
+typedef void (*ring_fn)(const float2*, float2*, const RingArgs, const CUtensorMap);
 typedef void (*plane_fn)(const float2*, float2*, const PlaneArgs);
 
 struct PlaneKernel {
@@ -75,11 +76,11 @@ struct PassLaunch {
     PlaneArgs pargs;    // PASS_PLANE
     PlaneKernel pk;     // PASS_PLANE
     int layout;
-    int tc;             // 1: tensor-core variant of the pass kernel
+    int tc;             // tensor-core variant of the pass kernel: 0 none, 1 + operand precision (TcPrec)
     int f64;            // 1: complex128 pass kernel
-    int pipe;           // 1: TMA-pipelined persistent variant (PipeArgs below)
-    PipeArgs pa;
-    long long B;        // pipe COL: outer extent of the tensor map (batch rows)
+    int ring;           // 1: tensor-copy ring kernel (RingArgs below)
+    RingArgs ra;
+    long long B;        // ring: outer extent of the tensor map (batch rows)
     int T;              // threads per pencil (fixed by the kernel: croft_threads_per_pencil)
     int grid;
     int block;
@@ -90,9 +91,8 @@ struct PassLaunch {
 // fused kernel for an ny x nz plane with the given cluster size (<= 0: the default one); NULL if none
 const PlaneKernel* find_plane_kernel(int ny, int nz, int cluster);
 
-// croft_pipe.cu, two size groups: the TMA-pipelined persistent pass kernel (NULL if not instantiated)
-pipe_fn lookup_pipe_kernel_group_0(int layout, int n);
-pipe_fn lookup_pipe_kernel_group_1(int layout, int n);
+// croft_ring.cu: the tensor-copy ring column kernel (NULL if not instantiated for n)
+ring_fn ring_kernel_for(int n);
 
 // croft_kernels.cu, one per size group (w: the COL tile width; ignored for ROW)
 pass_fn lookup_pass_kernel_group_0(int layout, int n, int w);
@@ -100,9 +100,10 @@ pass_fn lookup_pass_kernel_group_1(int layout, int n, int w);
 pass_fn lookup_pass_kernel_group_2(int layout, int n, int w);
 pass_fn lookup_pass_kernel_group_3(int layout, int n, int w);
 
-// croft_tc.cu: tensor-core pass kernels (NULL when n has no instantiation)
-pass_fn tc_pass_kernel_for(int layout, int n);
-void tc_dft16_matrix(unsigned char* out4096);  // B operand (hi | lo) in the kernels' smem layout
+// croft_tc.cu: tensor-core pass kernels (NULL when n has no instantiation); prec 0 = split
+// bf16, 1 = split fp16 with per-butterfly power-of-two scaling (TcPrec)
+pass_fn tc_pass_kernel_for(int layout, int n, int prec);
+void tc_dft16_matrix(unsigned char* out4096, int prec);  // B operand (hi | lo) in the kernels' smem layout
 
 // croft_alloc.cu: all library allocations (failure injection for tests)
 cudaError_t dev_alloc(void** p, size_t bytes);
@@ -127,12 +128,13 @@ cudaError_t launch_scale(const void* in, void* out, const void* g, long long n, 
 // croft_passes.cu
 extern int g_max_smem;  // the device's opt-in shared memory per block (set by plan creation)
 // Launch shape of one axis pass (tile width, block, grid, shared memory); false when no shape fits.
-bool shape_pass(PassLaunch& L, int layout, int n, long long M, long long ncols, bool tc = false, bool f64 = false,
+bool shape_pass(PassLaunch& L, int layout, int n, long long M, long long ncols, int tc = 0, bool f64 = false,
                 int want_w = 0);
 pass_fn pass_kernel_for(int layout, int n, int w);
 conv_fn conv_kernel_for(int n);
-pipe_fn pipe_kernel_for(int layout, int n);
-int pipe_blocks_per_sm(const PassLaunch& L);
+// Launch shape of a ring column pass (one persistent CTA per SM); false when the pass does not
+// qualify (length, odd stride, shared memory).
+bool shape_ring(PassLaunch& L, int n, long long M, long long ncols);
 cudaError_t prepare_pass(const PassLaunch& L);  // once per plan: shared-memory / cluster opt-ins, occupancy check
 // pdl: launch with programmatic stream serialisation (ignored for kernels that do not wait for it)
 cudaError_t launch_pass(const PassLaunch& L, const void* in, void* out, cudaStream_t s, bool pdl = false);

@@ -17,10 +17,10 @@ int g_max_smem = 0;
 // COL: W adjacent columns per CTA, W a multiple of 16 (128-byte rows).
 // Aim for ~256 threads per CTA and <= 100 KB of shared memory so that at
 // least two CTAs share an SM.
-bool shape_pass(PassLaunch& L, int layout, int n, long long M, long long ncols, bool tc, bool f64, int want_w) {
+bool shape_pass(PassLaunch& L, int layout, int n, long long M, long long ncols, int tc, bool f64, int want_w) {
     memset(&L, 0, sizeof(L));
     L.layout = layout;
-    L.tc = tc ? 1 : 0;
+    L.tc = tc;
     L.f64 = f64 ? 1 : 0;
     const long long es = f64 ? 16 : 8;  // bytes per element
     PassArgs& A = L.args;
@@ -53,9 +53,13 @@ bool shape_pass(PassLaunch& L, int layout, int n, long long M, long long ncols, 
         A.W = W;
         L.smem = (int)((A.tw_pad + (long long)n * W) * es);
     }
-    if (croft_make_sched(n).count <= 1 && !tc) L.smem = 0;  // single-stage kernels touch no shared memory
-    if (tc) L.smem += 4096;                                  // + the DFT-16 operand
     L.block = A.W * T;
+    if (croft_make_sched(n).count <= 1 && !tc) L.smem = 0;  // single-stage kernels touch no shared memory
+    if (tc) {
+        // the A operands (128 bytes per thread) reuse the pass tile, which may be smaller
+        const long long tile = L.smem - (long long)A.tw_pad * es, ops = 128LL * L.block;
+        L.smem = (int)((long long)A.tw_pad * es + 4096 + (tile > ops ? tile : ops));  // + the DFT-16 operand
+    }
     if (tc && (L.block % 128) != 0) return false;           // 128-butterfly GEMM groups
     if (L.block > max_threads) return false;
     long long grid = (ncols + A.W - 1) / A.W;
@@ -63,12 +67,6 @@ bool shape_pass(PassLaunch& L, int layout, int n, long long M, long long ncols, 
     L.grid = (int)grid;
     if (L.smem > g_max_smem) return false;
     return true;
-}
-
-pipe_fn pipe_kernel_for(int layout, int n) {
-    pipe_fn f = lookup_pipe_kernel_group_0(layout, n);
-    if (!f) f = lookup_pipe_kernel_group_1(layout, n);
-    return f;
 }
 
 // cuTensorMapEncodeTiled through the runtime's driver entry point (no link to libcuda).
@@ -87,31 +85,60 @@ static PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder() {
     return fn;
 }
 
-// 3D map over the source of a COL pass: dims {M, n, B} (innermost first), box {W, box_rows, 1}.
-static bool encode_col_map(const PassLaunch& L, const float2* src, CUtensorMap* map) {
+// 3D map over the source of a ring column pass: dims {M, n, B} (innermost first), box
+// {16 columns, box_rows, 1}; 8-byte elements (one complex64 each), no swizzle.
+static bool encode_ring_map(const PassLaunch& L, const float2* src, CUtensorMap* map) {
     PFN_cuTensorMapEncodeTiled_v12000 enc = tensor_map_encoder();
     if (!enc) return false;
-    const cuuint64_t dims[3] = {(cuuint64_t)L.pa.M, (cuuint64_t)L.args.n, (cuuint64_t)L.B};
-    const cuuint64_t strides[2] = {(cuuint64_t)L.pa.M * sizeof(float2), (cuuint64_t)L.pa.M * L.args.n * sizeof(float2)};
-    const cuuint32_t box[3] = {(cuuint32_t)L.pa.W, (cuuint32_t)L.pa.box_rows, 1};
+    const cuuint64_t dims[3] = {(cuuint64_t)L.ra.M, (cuuint64_t)L.args.n, (cuuint64_t)L.B};
+    const cuuint64_t strides[2] = {(cuuint64_t)L.ra.M * sizeof(float2), (cuuint64_t)L.ra.M * L.args.n * sizeof(float2)};
+    const cuuint32_t box[3] = {(cuuint32_t)kRingTileWidth, (cuuint32_t)L.ra.box_rows, 1};
     const cuuint32_t estr[3] = {1, 1, 1};
     return enc(map, CU_TENSOR_MAP_DATA_TYPE_FLOAT64, 3, (void*)src, dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
-               CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+               CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
 }
 
-int pipe_blocks_per_sm(const PassLaunch& L) {
-    pipe_fn f = pipe_kernel_for(L.layout, L.args.n);
-    if (!f) return 0;
+bool shape_ring(PassLaunch& L, int n, long long M, long long ncols) {
+    memset(&L, 0, sizeof(L));
+    ring_fn f = ring_kernel_for(n);
+    // tensor copies need 16-byte strides (M even) and 16-byte aligned column starts (tiles of 16)
+    if (!f || croft_threads_per_pencil(n) != 32 || M < 2 || (M % 2) != 0 || ncols % M != 0) return false;
+    L.kind = PASS_AXIS;
+    L.layout = LAYOUT_COL;
+    L.ring = 1;
+    L.T = 32;
+    L.args.n = n;
+    L.args.M = M;
+    L.args.ncols = ncols;
+    L.args.W = kRingTileWidth;
+    RingArgs& R = L.ra;
+    R.M = M;
+    R.tiles_per_row = (M + kRingTileWidth - 1) / kRingTileWidth;
+    L.B = ncols / M;
+    R.ntiles = L.B * R.tiles_per_row;
+    if (R.ntiles > 0x7fffffffLL || L.B > 0x7fffffffLL) return false;
+    int k = (n + 255) / 256;  // rows per box: the largest divisor of n that is <= 256
+    while (n % k) ++k;
+    R.box_rows = n / k;
+    R.tw_pad = ((n + 15) / 16) * 16;
+    R.wait_cycles = 4000000000LL;  // ~2 s at the maximum SM clock
+    L.block = 1024;
+    L.smem = (R.tw_pad + 3 * n * kRingTileWidth) * (int)sizeof(float2) + 128;  // + alignment of the tiles
+    if (L.smem > g_max_smem) return false;
     if (L.smem > 48 * 1024 && cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, L.smem) != cudaSuccess) {
         cudaGetLastError();
-        return 0;
+        return false;
     }
-    int n = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, f, L.block, L.smem) != cudaSuccess) {
+    int per_sm = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, f, L.block, L.smem) != cudaSuccess || per_sm < 1) {
         cudaGetLastError();
-        return 0;
+        return false;
     }
-    return n;
+    int dev = 0, sms = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    L.grid = (int)(R.ntiles < (long long)sms ? R.ntiles : (long long)sms);
+    return L.grid > 0 && tensor_map_encoder() != nullptr;
 }
 
 pass_fn pass_kernel_for(int layout, int n, int w) {
@@ -170,7 +197,7 @@ static cudaError_t launch_ex(void (*f)(P...), const PassLaunch& L, cudaStream_t 
     return cudaLaunchKernelEx(&cfg, f, args...);
 }
 
-bool pass_supports_pdl(const PassLaunch& L) { return !L.tc && !L.pipe; }
+bool pass_supports_pdl(const PassLaunch& L) { return !L.tc; }
 
 cudaError_t prepare_pass(const PassLaunch& L) {
     if (L.kind == PASS_PLANE) {
@@ -188,9 +215,9 @@ cudaError_t prepare_pass(const PassLaunch& L) {
         if (e != cudaSuccess) return e;
         return nclusters > 0 ? cudaSuccess : cudaErrorInvalidConfiguration;
     }
-    if (L.pipe) {
-        pipe_fn f = pipe_kernel_for(L.layout, L.args.n);
-        if (!f || (L.layout == LAYOUT_COL && !tensor_map_encoder())) return cudaErrorInvalidValue;
+    if (L.ring) {
+        ring_fn f = ring_kernel_for(L.args.n);
+        if (!f || !tensor_map_encoder()) return cudaErrorInvalidValue;
         if (L.smem <= 48 * 1024) return cudaSuccess;
         return cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, L.smem);
     }
@@ -200,7 +227,7 @@ cudaError_t prepare_pass(const PassLaunch& L) {
         if (L.smem <= 48 * 1024) return cudaSuccess;
         return cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, L.smem);
     }
-    pass_fn f = L.tc ? tc_pass_kernel_for(L.layout, L.args.n) : pass_kernel_for(L.layout, L.args.n, L.args.W);
+    pass_fn f = L.tc ? tc_pass_kernel_for(L.layout, L.args.n, L.tc - 1) : pass_kernel_for(L.layout, L.args.n, L.args.W);
     if (!f) return cudaErrorInvalidValue;
     if (L.smem <= 48 * 1024) return cudaSuccess;
     return cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, L.smem);
@@ -220,19 +247,20 @@ cudaError_t launch_pass(const PassLaunch& L, const void* vin, void* vout, cudaSt
         cudaLaunchConfig_t cfg = plane_config(L, s, attr, pdl);
         return cudaLaunchKernelEx(&cfg, L.pk.fn, in, out, L.pargs);
     }
-    if (L.pipe) {
-        pipe_fn f = pipe_kernel_for(L.layout, L.args.n);
+    if (L.ring) {
+        ring_fn f = ring_kernel_for(L.args.n);
         if (!f) return cudaErrorInvalidValue;
         CUtensorMap map;
         memset(&map, 0, sizeof(map));
-        if (L.layout == LAYOUT_COL && !encode_col_map(L, in, &map)) return cudaErrorInvalidValue;
-        PipeArgs pa = L.pa;
-        pa.isign = L.args.isign;
-        f<<<L.grid, L.block, L.smem, s>>>(in, out, pa, map);
-        return cudaGetLastError();
+        if (!encode_ring_map(L, in, &map)) return cudaErrorInvalidValue;
+        RingArgs ra = L.ra;
+        ra.isign = L.args.isign;
+        ra.tw = L.args.tw;
+        ra.status = L.args.status;
+        return launch_ex(f, L, s, pdl, in, out, ra, map);
     }
     if (L.tc) {
-        pass_fn f = tc_pass_kernel_for(L.layout, L.args.n);
+        pass_fn f = tc_pass_kernel_for(L.layout, L.args.n, L.tc - 1);
         if (!f) return cudaErrorInvalidValue;
         f<<<L.grid, L.block, L.smem, s>>>(in, out, L.args);
         return cudaGetLastError();

@@ -115,58 +115,6 @@ std::string batch_describe(const croft_plan_s* p);
 
 // (shape_pass and the device's shared-memory limit g_max_smem live in croft_passes.cu)
 
-// Launch shape of a TMA-pipelined persistent pass (croft_pipe_kernel.cuh): two tile
-// buffers per CTA, 128-byte aligned; as many resident CTAs as fit, capped by the tiles.
-static bool shape_pipe(PassLaunch& L, int layout, int n, long long M, long long ncols) {
-    memset(&L, 0, sizeof(L));
-    L.kind = PASS_AXIS;
-    L.layout = layout;
-    L.pipe = 1;
-    L.args.n = n;
-    L.args.M = M;
-    L.args.ncols = ncols;
-    const int T = croft_threads_per_pencil(n);
-    L.T = T;
-    PipeArgs& P = L.pa;
-    P.tw_pad = ((n + 15) / 16) * 16;
-    int W, buf;
-    if (layout == LAYOUT_ROW) {
-        W = (256 + T - 1) / T;
-        while (W > 1 && W * T > 512) --W;
-        buf = W * croft_row_ld(n);
-        P.ncols = ncols;
-        P.ntiles = (ncols + W - 1) / W;
-        P.M = 1;
-        L.B = 1;
-    } else {
-        W = 16;
-        while (W < 64 && 2 * W * T <= 256) W *= 2;
-        if (W * T > 512) return false;
-        buf = n * W;
-        P.M = M;
-        P.tiles_per_row = (M + W - 1) / W;
-        L.B = ncols / M;
-        P.ntiles = L.B * P.tiles_per_row;
-        int k = (n + 255) / 256;
-        while (n % k) ++k;
-        P.box_rows = n / k;
-    }
-    P.W = W;
-    P.buf_elems = ((buf + 15) / 16) * 16;
-    L.args.W = W;
-    L.block = W * T;
-    L.smem = (P.tw_pad + 2 * P.buf_elems) * (int)sizeof(float2);
-    if (L.smem > g_max_smem || L.block > 512) return false;
-    const int bps = pipe_blocks_per_sm(L);
-    if (bps < 1) return false;
-    int dev = 0, sms = 0;
-    cudaGetDevice(&dev);
-    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    const long long g = (long long)sms * bps;
-    L.grid = (int)(P.ntiles < g ? P.ntiles : g);
-    return L.grid > 0;
-}
-
 extern "C" {
 
 const char* croft_status_string(croft_status s) {
@@ -228,15 +176,18 @@ static croft_status add_axis_pass(croft_plan p, int axis, int x0 = 0, int nxs = 
     // element stride of the axis; a unit stride means the pencils are contiguous rows
     const long long M = (axis == 2) ? 1 : (axis == 1 ? (long long)nz : (long long)ny * nz);
     const int layout = M == 1 ? LAYOUT_ROW : LAYOUT_COL;
-    // the TMA-pipelined kernel is opt-in (CROFT_PIPE=1): measured slower than the plain kernel so far
-    const char* pe = getenv("CROFT_PIPE");
-    const bool allow_pipe = pe && pe[0] == '1';
     const bool f64 = p->dtype == CROFT_C2C_F64;
-    if (allow_pipe && !f64 && !p->axis_tc[axis] && pipe_kernel_for(layout, n) && (layout == LAYOUT_ROW || (M % 2) == 0) &&
-        !croft_even_pow2_pass(n, layout, 8)) {  // (the pipelined kernel runs the default schedule)
+    // Column passes of 32-thread pencils (270..512 points) whose axis elements lie more than
+    // 16 KB apart (the x pass) run the tensor-copy ring kernel; CROFT_RING=1 takes it for
+    // every such column pass, CROFT_RING=0 for none (both for measurement).
+    const char* re = getenv("CROFT_RING");
+    const bool ring_pass = layout == LAYOUT_COL && !f64 && !p->axis_tc[axis] &&
+                           (re ? re[0] == '1' : croft_ring_default(n, 8, M * 8));
+    if (ring_pass) {
         PassLaunch L;
-        if (shape_pipe(L, layout, n, M, N / n)) {
-            L.pa.tw = p->tw_dev[axis];
+        if (shape_ring(L, n, M, N / n)) {
+            L.args.tw = p->tw_dev[axis];
+            L.args.status = p->d_status;
             L.offset = offset;
             L.src_in = sin;
             L.group = grp;
@@ -250,7 +201,7 @@ static croft_status add_axis_pass(croft_plan p, int axis, int x0 = 0, int nxs = 
         }
     }
     PassLaunch L;
-    if (!shape_pass(L, layout, n, M, N / n, p->axis_tc[axis], f64)) return CROFT_ERR_UNSUPPORTED_SIZE;
+    if (!shape_pass(L, layout, n, M, N / n, p->axis_tc[axis] ? 1 + p->tc_prec : 0, f64)) return CROFT_ERR_UNSUPPORTED_SIZE;
     L.kind = PASS_AXIS;
     L.args.tw = p->tw_dev[axis];
     L.args.tw64 = f64 ? (const double2*)p->tw_dev[axis] : nullptr;
@@ -364,7 +315,9 @@ static void plan_conv(croft_plan p) {
 static croft_status create_impl(croft_plan* out, int nx, int ny, int nz, croft_dtype dtype, croft_schedule sched) {
     if (!out) return CROFT_ERR_INVALID_ARG;
     *out = NULL;
-    if (dtype != CROFT_C2C_F32 && dtype != CROFT_C2C_F32_TC_BF16X3 && dtype != CROFT_C2C_F64) return CROFT_ERR_INVALID_ARG;
+    if (dtype != CROFT_C2C_F32 && dtype != CROFT_C2C_F32_TC_BF16X3 && dtype != CROFT_C2C_F32_TC_FP16X3 &&
+        dtype != CROFT_C2C_F64)
+        return CROFT_ERR_INVALID_ARG;
     if (dtype == CROFT_C2C_F64) {
         // complex128: three-pass schedule on the instantiated lengths only
         if (sched == CROFT_SCHEDULE_PLANE_FUSED || sched == CROFT_SCHEDULE_SLAB_L2) return CROFT_ERR_UNSUPPORTED_SIZE;
@@ -403,14 +356,21 @@ static croft_status create_impl(croft_plan* out, int nx, int ny, int nz, croft_d
     p->conv_axis = -1;
     const char* pdl_env = getenv("CROFT_PDL");  // 0: ordinary stream ordering between passes (for measurement)
     p->pdl = !(pdl_env && pdl_env[0] == '0');
-    const bool want_tc = dtype == CROFT_C2C_F32_TC_BF16X3;
+    const bool want_tc = dtype == CROFT_C2C_F32_TC_BF16X3 || dtype == CROFT_C2C_F32_TC_FP16X3;
+    const int tc_prec = dtype == CROFT_C2C_F32_TC_FP16X3 ? 1 : 0;  // TcPrec
+    p->tc_prec = tc_prec;
     for (int axis = 0; axis < 3; ++axis) {
         const long long M = (axis == 2) ? 1 : (axis == 1 ? (long long)nz : (long long)ny * nz);
-        p->axis_tc[axis] = want_tc && tc_pass_kernel_for(M == 1 ? LAYOUT_ROW : LAYOUT_COL, p->dims[axis]) != NULL;
+        // an axis with a radix-16 stage runs it on the tensor cores, or the plan is refused (no
+        // silent FP32 stand-in); an axis without one has no stage to put there
+        const bool radix16 = p->dims[axis] % 16 == 0;
+        p->axis_tc[axis] = want_tc && radix16;
+        if (p->axis_tc[axis] && !tc_pass_kernel_for(M == 1 ? LAYOUT_ROW : LAYOUT_COL, p->dims[axis], tc_prec))
+            return fail(p, CROFT_ERR_UNSUPPORTED_SIZE);
     }
     if (want_tc) {
         unsigned char hb[4096];
-        tc_dft16_matrix(hb);
+        tc_dft16_matrix(hb, tc_prec);
         if (dev_alloc((void**)&p->tc_b, 4096) != cudaSuccess) return fail(p, CROFT_ERR_OOM);
         if (dev_alloc((void**)&p->d_status, sizeof(int)) != cudaSuccess) return fail(p, CROFT_ERR_OOM);
         if (cudaMemcpy(p->tc_b, hb, 4096, cudaMemcpyHostToDevice) != cudaSuccess) return fail(p, CROFT_ERR_CUDA);
@@ -533,7 +493,7 @@ int croft_plan_describe(croft_plan plan, char* buf, int cap) {
             continue;
         }
         snprintf(tmp, sizeof(tmp), " | %s:%s%s%s n=%d radix=", an[plan->pass_axis[i]], L.layout == LAYOUT_ROW ? "row" : "col",
-                 L.tc ? "+tc" : "", L.pipe ? "+tma" : "", L.args.n);
+                 L.tc ? (L.tc == 2 ? "+tc_fp16x3" : "+tc_bf16x3") : "", L.ring ? "+ring" : "", L.args.n);
         s += tmp;
         CroftSched sc = L.tc ? croft_make_sched_tc(L.args.n) : croft_pass_sched(L.args.n, L.layout, L.f64 ? 16 : 8);
         for (int st = 0; st < sc.count; ++st) {
@@ -558,6 +518,14 @@ int croft_plan_describe(croft_plan plan, char* buf, int cap) {
         buf[m] = 0;
     }
     return (int)s.size();
+}
+
+int croft_plan_tc_axes(croft_plan plan) {
+    if (!plan || plan->batch) return 0;
+    int m = 0;
+    for (size_t i = 0; i < plan->passes.size(); ++i)
+        if (plan->passes[i].tc && plan->pass_axis[i] >= 0 && plan->pass_axis[i] <= 2) m |= 1 << plan->pass_axis[i];
+    return m;
 }
 
 size_t croft_plan_workspace_bytes(croft_plan plan) {
@@ -742,6 +710,75 @@ croft_status croft_exec_convolve(croft_plan plan, const void* in, void* out, con
 
 croft_status croft_exec_forward(croft_plan plan, const void* in, void* out, void* stream) {
     return exec_dir(plan, in, out, stream, 1.0f);
+}
+
+croft_status croft_exec_axes(croft_plan plan, const void* in, void* out, int axes, int direction, void* stream) {
+    if (!plan || !in || !out || plan->batch || (axes & ~7) || (direction != 1 && direction != -1))
+        return CROFT_ERR_INVALID_ARG;
+    if (((uintptr_t)in & 15) || ((uintptr_t)out & 15)) return CROFT_ERR_INVALID_ARG;
+    const long long N = (long long)plan->dims[0] * plan->dims[1] * plan->dims[2];
+    const size_t bytes = (size_t)N * elem_bytes(plan);
+    if (in != out && overlaps(in, bytes, out, bytes)) return CROFT_ERR_INVALID_ARG;
+    // one launch per axis, over the whole grid (the three-pass schedule) - anything else cannot
+    // run a subset of its axes
+    for (size_t i = 0; i < plan->passes.size(); ++i)
+        if (plan->passes[i].kind != PASS_AXIS || plan->passes[i].offset != 0 || plan->pass_axis[i] > 2)
+            return CROFT_ERR_INVALID_ARG;
+    cudaStream_t s = (cudaStream_t)stream;
+    if (plan->d_status && cudaMemsetAsync(plan->d_status, 0, sizeof(int), s) != cudaSuccess) {
+        cudaGetLastError();
+        return CROFT_ERR_CUDA;
+    }
+    const float isign = direction == -1 ? 1.0f : -1.0f;
+    bool started = false, first = true;
+    for (size_t i = 0; i < plan->passes.size(); ++i) {
+        if (!(axes & (1 << plan->pass_axis[i]))) continue;
+        PassLaunch L = plan->passes[i];
+        L.args.isign = isign;
+        const bool pdl = plan->pdl && started;
+        started = true;
+        if (launch_pass(L, first ? in : out, out, s, pdl) != cudaSuccess) {
+            cudaGetLastError();
+            return CROFT_ERR_CUDA;
+        }
+        first = false;
+    }
+    // no pass ran (no selected axis longer than 1): the selected transforms are the identity
+    if (first && in != out && cudaMemcpyAsync(out, in, bytes, cudaMemcpyDeviceToDevice, s) != cudaSuccess) {
+        cudaGetLastError();
+        return CROFT_ERR_CUDA;
+    }
+    plan->ev_count = 0;
+    plan->ran = true;
+    return CROFT_OK;
+}
+
+croft_status croft_transpose_blocks(const void* in, void* out, long long d0, long long d1, long long block_bytes,
+                                    void* stream) {
+    if (!in || !out || d0 < 1 || d1 < 1 || block_bytes < 1) return CROFT_ERR_INVALID_ARG;
+    const size_t bytes = (size_t)d0 * (size_t)d1 * (size_t)block_bytes;
+    if (overlaps(in, bytes, out, bytes)) return CROFT_ERR_INVALID_ARG;
+    cudaStream_t s = (cudaStream_t)stream;
+    const char* src = (const char*)in;
+    char* dst = (char*)out;
+    const size_t w = (size_t)block_bytes;
+    // out[j][i] = in[i][j]: one pitched copy per index of the shorter dimension
+    if (d1 <= d0) {
+        for (long long j = 0; j < d1; ++j)  // column j of `in` -> row j of `out`
+            if (cudaMemcpy2DAsync(dst + (size_t)j * d0 * w, w, src + (size_t)j * w, (size_t)d1 * w, w, (size_t)d0,
+                                  cudaMemcpyDeviceToDevice, s) != cudaSuccess) {
+                cudaGetLastError();
+                return CROFT_ERR_CUDA;
+            }
+    } else {
+        for (long long i = 0; i < d0; ++i)  // row i of `in` -> column i of `out`
+            if (cudaMemcpy2DAsync(dst + (size_t)i * w, (size_t)d0 * w, src + (size_t)i * d1 * w, w, w, (size_t)d1,
+                                  cudaMemcpyDeviceToDevice, s) != cudaSuccess) {
+                cudaGetLastError();
+                return CROFT_ERR_CUDA;
+            }
+    }
+    return CROFT_OK;
 }
 
 }  // extern "C"

@@ -32,6 +32,7 @@ struct croft_plan_s {
     unsigned char* tc_b;              // tensor-core plans: DFT-16 operand (4 KB), else NULL
     int* d_status;                    // tensor-core plans: device status word, else NULL
     bool axis_tc[3];                  // axis runs the tensor-core pass kernel
+    int tc_prec;                      // tensor-core operand precision (TcPrec) of such axes
     croft::PassLaunch conv;           // fused convolution pass (croft_conv_kernel.cuh), valid when conv_fused
     int conv_axis;                    // its axis (the plan's last pass)
     bool conv_fused;                  // false: croft_exec_convolve runs F, a multiply and B instead

@@ -207,3 +207,12 @@ CROFT_HD constexpr int croft_pass_minb(int n, int es) { return (es == 8 && n == 
 // Column-tile width of the fused convolution pass: the same as a COL pass (8 columns
 // measured slower at every size from 384 to 512: 480^3 774 vs 690 us).
 CROFT_HD constexpr int croft_conv_width(int n, int es) { return croft_col_width(n, es); }
+
+// Whether a column pass of a length-n axis whose elements lie stride_bytes apart runs the
+// tensor-copy ring kernel (croft_ring_kernel.cuh) by default: never so far.  Measured per pass
+// against the plain kernels (CUDA events, L2 flushed): x pass 512^3 0.487 vs 0.488 ms, 480^3
+// 0.435 vs 0.348, 384x360x320 0.250 vs 0.127, 320^3 0.119 vs 0.123; y pass 512^3 0.479 vs
+// 0.399 (the narrow tile).  CROFT_RING=1 selects it for every column pass it can serve.
+CROFT_HD constexpr bool croft_ring_default(int n, int es, long long stride_bytes) {
+    return false && es == 8 && croft_threads_per_pencil(n) == 32 && stride_bytes > 16 * 1024;
+}

@@ -3,56 +3,55 @@
 #include <string.h>
 
 #include "croft_tc_kernel.cuh"
+#include "croft_tc_operand.h"
 
 namespace croft {
 
-pass_fn tc_pass_kernel_for(int layout, int n) {
+// Every length <= 1024 with a factor 16 (a radix-16 stage) and 2^a 3^b 5^c: the tensor-core
+// stages need at most one butterfly per thread (N / 16 <= threads per pencil), which holds up
+// to 1024 points.  Compiled in four groups (-DCROFT_TC_GROUP=0..3) so they build in parallel.
+#define CROFT_TC_SIZES_0(X) X(16) X(80) X(160) X(288) X(432) X(640) X(864)
+#define CROFT_TC_SIZES_1(X) X(32) X(96) X(192) X(320) X(480) X(720) X(960)
+#define CROFT_TC_SIZES_2(X) X(48) X(128) X(240) X(384) X(512) X(768) X(1024)
+#define CROFT_TC_SIZES_3(X) X(64) X(144) X(256) X(400) X(576) X(800)
+
+#ifdef CROFT_TC_GROUP
+#define CROFT_TCAT_(a, b) a##b
+#define CROFT_TCAT(a, b) CROFT_TCAT_(a, b)
+
+pass_fn CROFT_TCAT(lookup_tc_kernel_group_, CROFT_TC_GROUP)(int layout, int n, int prec) {
+#define CROFT_TC_CASE(N)                                                                                     \
+    case N:                                                                                                  \
+        if (prec == TC_BF16X3)                                                                               \
+            return layout == LAYOUT_ROW ? croft_pass_kernel_tc<LAYOUT_ROW, N, TC_BF16X3>                     \
+                                        : croft_pass_kernel_tc<LAYOUT_COL, N, TC_BF16X3>;                    \
+        return layout == LAYOUT_ROW ? croft_pass_kernel_tc<LAYOUT_ROW, N, TC_FP16X3>                         \
+                                    : croft_pass_kernel_tc<LAYOUT_COL, N, TC_FP16X3>;
     switch (n) {
-        case 256: return layout == LAYOUT_ROW ? croft_pass_kernel_tc<LAYOUT_ROW, 256> : croft_pass_kernel_tc<LAYOUT_COL, 256>;
-        case 512: return layout == LAYOUT_ROW ? croft_pass_kernel_tc<LAYOUT_ROW, 512> : croft_pass_kernel_tc<LAYOUT_COL, 512>;
+        CROFT_TCAT(CROFT_TC_SIZES_, CROFT_TC_GROUP)(CROFT_TC_CASE)
         default: return nullptr;
     }
+#undef CROFT_TC_CASE
 }
 
-static unsigned short bf16_bits_rn(float x) {
-    unsigned int u;
-    memcpy(&u, &x, 4);
-    const unsigned int lsb = (u >> 16) & 1u;
-    u += 0x7FFFu + lsb;  // round to nearest even (inputs are finite)
-    return (unsigned short)(u >> 16);
-}
+#else  // the lookup and the DFT-16 operands (one translation unit)
 
-static float bf16_value(unsigned short b) {
-    unsigned int u = (unsigned int)b << 16;
-    float f;
-    memcpy(&f, &u, 4);
+pass_fn lookup_tc_kernel_group_0(int layout, int n, int prec);
+pass_fn lookup_tc_kernel_group_1(int layout, int n, int prec);
+pass_fn lookup_tc_kernel_group_2(int layout, int n, int prec);
+pass_fn lookup_tc_kernel_group_3(int layout, int n, int prec);
+
+pass_fn tc_pass_kernel_for(int layout, int n, int prec) {
+    if (prec != TC_BF16X3 && prec != TC_FP16X3) return nullptr;
+    pass_fn f = lookup_tc_kernel_group_0(layout, n, prec);
+    if (!f) f = lookup_tc_kernel_group_1(layout, n, prec);
+    if (!f) f = lookup_tc_kernel_group_2(layout, n, prec);
+    if (!f) f = lookup_tc_kernel_group_3(layout, n, prec);
     return f;
 }
 
-// B operand of the radix-16 GEMM, B[n][k] (n = output, k = input; re parts then im parts):
-//   n < 16 : B[n][j] = C[n][j],  B[n][16+j] = -S[n][j]
-//   n >= 16: B[n][j] = S[n-16][j], B[n][16+j] = C[n-16][j]
-// with C + iS = exp(-2 pi i n j / 16), evaluated in float64 with (n j) mod 16 reduced
-// in integers; split into bf16 hi = rn(B) and lo = rn(B - hi).  Layout: K-major,
-// no-swizzle core matrices (tc_cm_offset), hi in bytes [0, 2048), lo in [2048, 4096).
-void tc_dft16_matrix(unsigned char* out) {
-    memset(out, 0, 4096);
-    for (int n = 0; n < 32; ++n)
-        for (int k = 0; k < 32; ++k) {
-            const int on = n & 15, ik = k & 15;
-            const int r = (on * ik) % 16;
-            const double ang = 2.0 * M_PI * (double)r / 16.0;
-            const double C = (r % 4 == 0) ? (r == 0 ? 1.0 : (r == 8 ? -1.0 : 0.0)) : cos(ang);
-            const double Sv = (r % 4 == 0) ? (r == 4 ? -1.0 : (r == 12 ? 1.0 : 0.0)) : -sin(ang);
-            double v;
-            if (n < 16) v = (k < 16) ? C : -Sv;
-            else v = (k < 16) ? Sv : C;
-            const unsigned short hi = bf16_bits_rn((float)v);
-            const unsigned short lo = bf16_bits_rn((float)(v - (double)bf16_value(hi)));
-            const int off = tc_cm_offset(n, k);
-            memcpy(out + off, &hi, 2);
-            memcpy(out + 2048 + off, &lo, 2);
-        }
-}
+void tc_dft16_matrix(unsigned char* out, int prec) { tc_dft16_operand(out, prec == TC_FP16X3); }
+
+#endif  // CROFT_TC_GROUP
 
 }  // namespace croft

@@ -8,10 +8,19 @@
 // so 128 butterflies form a 128 x 32 x 32 GEMM: M = 128 rows (butterflies),
 // N = 32 (re/im of the 16 outputs), K = 32 (re/im of the 16 inputs).
 //
-// Precision (split operands): each operand x is stored as hi = bf16(x) and
-// lo = bf16(x - hi); the products hi*hi + hi*lo + lo*hi are accumulated in
-// FP32 (the lo*lo term, ~2^-16 relative, is dropped).  bf16 keeps FP32's
-// exponent range, so no pre-scaling is needed.
+// Precision (split operands), two variants:
+//  * bf16x3: each operand x is stored as hi = bf16(x) and lo = bf16(x - hi);
+//    the products hi*hi + hi*lo + lo*hi are accumulated in FP32 (the lo*lo
+//    term, ~2^-16 relative, is dropped).  bf16 keeps FP32's exponent range, so
+//    no pre-scaling is needed; hi + lo carries ~16 significant bits.
+//  * fp16x3: the same three products with fp16 halves (11-bit significands,
+//    so hi + lo carries ~22 bits and the dropped lo*lo term is ~2^-22).  fp16's
+//    range is narrow, so each butterfly's 16 inputs are first scaled by a power
+//    of two that puts their largest real or imaginary part in [2^14, 2^15)
+//    (exact), and the 16 outputs are scaled back after the product (exact: the
+//    radix-16 DFT is linear, one butterfly per GEMM row).  This is the
+//    per-pencil power-of-two scaling of the split-fp16 scheme, applied per
+//    butterfly, the finest granularity one GEMM row allows.
 //
 // Hardware path (sm_103a): operands in shared memory in the K-major,
 // no-swizzle core-matrix layout (8 rows x 16 bytes per core matrix; core
@@ -29,18 +38,16 @@
 #pragma once
 #include <type_traits>
 #include <cuda_bf16.h>
+#include <cuda_fp16.h>
 
 #include "croft_fft_core.cuh"
 #include "croft_internal.h"
+#include "croft_tc_operand.h"
 
 namespace croft {
 
 __device__ __forceinline__ uint32_t smem_addr(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
 
-// Byte offset of element (row r, k) of a K = 32 bf16 K-major operand, no swizzle.
-__host__ __device__ constexpr int tc_cm_offset(int r, int k) {
-    return (r / 8) * 512 + (k / 8) * 128 + (r % 8) * 16 + (k % 8) * 2;
-}
 
 __device__ __forceinline__ uint64_t tc_desc(uint32_t saddr) {
     uint64_t d = 0;
@@ -51,14 +58,41 @@ __device__ __forceinline__ uint64_t tc_desc(uint32_t saddr) {
     return d;                         // base offset 0, no swizzle
 }
 
-// kind::f16 instruction descriptor: D f32, A and B bf16, both K-major, N = 32, M = 128.
-constexpr uint32_t kTcIdesc = (1u << 4) | (1u << 7) | (1u << 10) | ((32u >> 3) << 17) | ((128u >> 4) << 24);
+// Operand precision of the tensor-core stage (PassLaunch::tc - 1).
+enum TcPrec { TC_BF16X3 = 0, TC_FP16X3 = 1 };
 
+// kind::f16 instruction descriptor: D f32, A and B of one type (bf16: bits 7-9 and 10-12 = 1;
+// fp16: 0), both K-major, N = 32, M = 128.
+template <int PREC>
+__host__ __device__ constexpr uint32_t tc_idesc() {
+    return (1u << 4) | (PREC == TC_BF16X3 ? (1u << 7) | (1u << 10) : 0u) | ((32u >> 3) << 17) | ((128u >> 4) << 24);
+}
+
+template <int PREC>
 __device__ __forceinline__ void tc_mma(uint32_t tmem_d, uint64_t a, uint64_t b, uint32_t accumulate) {
     asm volatile(
         "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
         " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(tmem_d),
-        "l"(a), "l"(b), "r"(kTcIdesc), "r"(accumulate));
+        "l"(a), "l"(b), "r"(tc_idesc<PREC>()), "r"(accumulate));
+}
+
+// Split a pair of floats into hi = rn(x) and lo = rn(x - hi) halves of the precision (packed
+// two per 32-bit word, the first value in the low half).
+template <int PREC>
+__device__ __forceinline__ void tc_split2(float a, float b, uint32_t& hi, uint32_t& lo) {
+    if constexpr (PREC == TC_BF16X3) {
+        const __nv_bfloat162 h = __floats2bfloat162_rn(a, b);
+        const float2 hf = __bfloat1622float2(h);
+        const __nv_bfloat162 l = __floats2bfloat162_rn(a - hf.x, b - hf.y);
+        hi = *reinterpret_cast<const uint32_t*>(&h);
+        lo = *reinterpret_cast<const uint32_t*>(&l);
+    } else {
+        const __half2 h = __floats2half2_rn(a, b);
+        const float2 hf = __half22float2(h);
+        const __half2 l = __floats2half2_rn(a - hf.x, b - hf.y);
+        hi = *reinterpret_cast<const uint32_t*>(&h);
+        lo = *reinterpret_cast<const uint32_t*>(&l);
+    }
 }
 
 // Bounded wait for the mbarrier phase with the given parity; false if it never completed.
@@ -98,17 +132,19 @@ struct TcCtx {
     int* status;          // device status word (timeout), may be null
 };
 
-// Radix-16 stage S of the (Tc16Sched) schedule on the tensor cores; one butterfly per thread.
-template <class SchedT, int S, int T, class Src, class Dst>
-__device__ __forceinline__ void fft_stage_tc16(const Src& src, const Dst& dst, const float2* stw, int lane, bool ok,
+// Radix-16 stage S of the (Tc16Sched) schedule on the tensor cores; at most one butterfly per
+// thread (threads past the N/16 butterflies of a pencil contribute zero GEMM rows).
+template <class SchedT, int S, int T, int PREC, class Src, class Dst>
+__device__ __forceinline__ void fft_stage_tc16(const Src& src, const Dst& dst, const float2* stw, int lane, bool ok_pencil,
                                                const TcCtx& tc, uint32_t parity) {
     constexpr int N = SchedT::N;
     constexpr CroftSched sc = SchedT::get();
     static_assert(sc.r[S] == 16, "tensor-core stage must be radix 16");
     constexpr int P = croft_sched_p(sc, S);
     constexpr int NB = N / 16;
-    static_assert(NB == T, "one butterfly per thread");
+    static_assert(NB <= T, "at most one butterfly per thread");
     const int b = lane;
+    const bool ok = ok_pencil && (NB == T || b < NB);
     float2 u[16];
     if (ok) {
 #pragma unroll
@@ -125,6 +161,18 @@ __device__ __forceinline__ void fft_stage_tc16(const Src& src, const Dst& dst, c
     }
     __syncthreads();  // every input of the stage read before the tile becomes the operand buffer
 
+    // fp16 operands: scale the butterfly by 2^sh so that its largest component lies in
+    // [2^14, 2^15) (exact; undone on the outputs below)
+    float scale = 1.f, unscale = 1.f;
+    if constexpr (PREC == TC_FP16X3) {
+        float m = 0.f;
+#pragma unroll
+        for (int j = 0; j < 16; ++j) m = fmaxf(m, fmaxf(fabsf(u[j].x), fabsf(u[j].y)));
+        const int eb = (int)((__float_as_uint(m) >> 23) & 0xff);  // biased exponent of the largest part
+        const int sh = min(141 - eb, 126);                         // 14 - (eb - 127), kept representable
+        scale = __uint_as_float((uint32_t)(sh + 127) << 23);
+        unscale = __uint_as_float((uint32_t)(127 - sh) << 23);
+    }
     // A row for this butterfly: k < 16 real parts, k >= 16 imaginary parts; hi and lo halves
     const int tid = threadIdx.x;
     const int g = tid >> 7, r = tid & 127;
@@ -132,16 +180,16 @@ __device__ __forceinline__ void fft_stage_tc16(const Src& src, const Dst& dst, c
     unsigned char* alo = tc.abuf + tc.groups * 8192 + g * 8192;
 #pragma unroll
     for (int kk = 0; kk < 4; ++kk) {
-        __nv_bfloat16 h[8], l[8];
+        uint32_t h[4], l[4];
 #pragma unroll
-        for (int e = 0; e < 8; ++e) {
+        for (int e = 0; e < 8; e += 2) {
             const int k = kk * 8 + e;
-            const float x = (k < 16) ? u[k].x : u[k - 16].y;
-            h[e] = __float2bfloat16_rn(x);
-            l[e] = __float2bfloat16_rn(x - __bfloat162float(h[e]));
+            const float x0 = ((k < 16) ? u[k].x : u[k - 16].y) * scale;
+            const float x1 = ((k + 1 < 16) ? u[k + 1].x : u[k + 1 - 16].y) * scale;
+            tc_split2<PREC>(x0, x1, h[e / 2], l[e / 2]);
         }
-        *(uint4*)(ahi + tc_cm_offset(r, kk * 8)) = *(const uint4*)h;
-        *(uint4*)(alo + tc_cm_offset(r, kk * 8)) = *(const uint4*)l;
+        *(uint4*)(ahi + tc_cm_offset(r, kk * 8)) = make_uint4(h[0], h[1], h[2], h[3]);
+        *(uint4*)(alo + tc_cm_offset(r, kk * 8)) = make_uint4(l[0], l[1], l[2], l[3]);
     }
     asm volatile("fence.proxy.async.shared::cta;");  // generic-proxy smem writes -> tensor core
     asm volatile("tcgen05.fence::before_thread_sync;");
@@ -156,10 +204,10 @@ __device__ __forceinline__ void fft_stage_tc16(const Src& src, const Dst& dst, c
             uint32_t acc = 0;
 #pragma unroll
             for (int ks = 0; ks < 2; ++ks) {  // K = 32 as two K = 16 steps
-                tc_mma(d, tc_desc(ah + ks * 256), tc_desc(tc.b_hi + ks * 256), acc);
+                tc_mma<PREC>(d, tc_desc(ah + ks * 256), tc_desc(tc.b_hi + ks * 256), acc);
                 acc = 1;
-                tc_mma(d, tc_desc(ah + ks * 256), tc_desc(tc.b_hi + 2048 + ks * 256), 1);
-                tc_mma(d, tc_desc(al + ks * 256), tc_desc(tc.b_hi + ks * 256), 1);
+                tc_mma<PREC>(d, tc_desc(ah + ks * 256), tc_desc(tc.b_hi + 2048 + ks * 256), 1);
+                tc_mma<PREC>(d, tc_desc(al + ks * 256), tc_desc(tc.b_hi + ks * 256), 1);
             }
         }
         asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(tc.mbar));
@@ -170,6 +218,10 @@ __device__ __forceinline__ void fft_stage_tc16(const Src& src, const Dst& dst, c
     const int warp = tid >> 5;
     tc_ld32(tc.tmem + 32 * (warp >> 2) + ((uint32_t)((warp & 3) * 32) << 16), d);
     asm volatile("tcgen05.fence::before_thread_sync;");
+    if constexpr (PREC == TC_FP16X3) {
+#pragma unroll
+        for (int i = 0; i < 32; ++i) d[i] *= unscale;
+    }
     if (ok) {
         const int k = (P == 1) ? 0 : b % P;
         const int o = (b - k) * 16 + k;
@@ -204,12 +256,12 @@ struct TcStageInfo {
 };
 
 // One stage with the given operands: radix-16 stages on the tensor cores, others on CUDA cores.
-template <class SchedT, int S, int T, class Src, class Dst>
+template <class SchedT, int S, int T, int PREC, class Src, class Dst>
 __device__ __forceinline__ void tc_run_stage(const Src& src, const Dst& dst, const float2* stw, int lane, bool ok,
                                              const TcCtx& tc, int tc_index) {
     using I = TcStageInfo<SchedT, S>;
     if constexpr (I::tc) {
-        fft_stage_tc16<SchedT, S, T>(src, dst, stw, lane, ok, tc, (uint32_t)(tc_index & 1));
+        fft_stage_tc16<SchedT, S, T, PREC>(src, dst, stw, lane, ok, tc, (uint32_t)(tc_index & 1));
     } else if constexpr (I::first) {
         fft_stage_s<SchedT, S, T>(src, NoBarrier{}, dst, stw, lane, ok);
     } else {
@@ -217,7 +269,7 @@ __device__ __forceinline__ void tc_run_stage(const Src& src, const Dst& dst, con
     }
 }
 
-template <class SchedT, int S, int LAYOUT, int T>
+template <class SchedT, int S, int LAYOUT, int T, int PREC>
 __device__ __forceinline__ void tc_stages(const float2* gin, float2* gout, float2* tile, const float2* stw,
                                           const PassArgs& A, int c, int lane, bool ok, long long M, const TcCtx& tc,
                                           int tc_index) {
@@ -226,32 +278,33 @@ __device__ __forceinline__ void tc_stages(const float2* gin, float2* gout, float
     if constexpr (LAYOUT == LAYOUT_ROW) {
         const SmemRow sm{tile + c * row_ld(N)};
         if constexpr (I::first && I::last)
-            tc_run_stage<SchedT, S, T>(GlobalInUnit{gin, A.isign}, GlobalOutUnit{gout, A.isign}, stw, lane, ok, tc, tc_index);
+            tc_run_stage<SchedT, S, T, PREC>(GlobalInUnit{gin, A.isign}, GlobalOutUnit{gout, A.isign}, stw, lane, ok, tc, tc_index);
         else if constexpr (I::first)
-            tc_run_stage<SchedT, S, T>(GlobalInUnit{gin, A.isign}, sm, stw, lane, ok, tc, tc_index);
+            tc_run_stage<SchedT, S, T, PREC>(GlobalInUnit{gin, A.isign}, sm, stw, lane, ok, tc, tc_index);
         else if constexpr (I::last)
-            tc_run_stage<SchedT, S, T>(sm, GlobalOutUnit{gout, A.isign}, stw, lane, ok, tc, tc_index);
+            tc_run_stage<SchedT, S, T, PREC>(sm, GlobalOutUnit{gout, A.isign}, stw, lane, ok, tc, tc_index);
         else
-            tc_run_stage<SchedT, S, T>(sm, sm, stw, lane, ok, tc, tc_index);
+            tc_run_stage<SchedT, S, T, PREC>(sm, sm, stw, lane, ok, tc, tc_index);
     } else {
         const SmemCol sm{tile + c, A.W};
         if constexpr (I::first && I::last)
-            tc_run_stage<SchedT, S, T>(GlobalIn{gin, M, A.isign}, GlobalOut{gout, M, A.isign}, stw, lane, ok, tc, tc_index);
+            tc_run_stage<SchedT, S, T, PREC>(GlobalIn{gin, M, A.isign}, GlobalOut{gout, M, A.isign}, stw, lane, ok, tc, tc_index);
         else if constexpr (I::first)
-            tc_run_stage<SchedT, S, T>(GlobalIn{gin, M, A.isign}, sm, stw, lane, ok, tc, tc_index);
+            tc_run_stage<SchedT, S, T, PREC>(GlobalIn{gin, M, A.isign}, sm, stw, lane, ok, tc, tc_index);
         else if constexpr (I::last)
-            tc_run_stage<SchedT, S, T>(sm, GlobalOut{gout, M, A.isign}, stw, lane, ok, tc, tc_index);
+            tc_run_stage<SchedT, S, T, PREC>(sm, GlobalOut{gout, M, A.isign}, stw, lane, ok, tc, tc_index);
         else
-            tc_run_stage<SchedT, S, T>(sm, sm, stw, lane, ok, tc, tc_index);
+            tc_run_stage<SchedT, S, T, PREC>(sm, sm, stw, lane, ok, tc, tc_index);
     }
     if constexpr (!I::last) {
         __syncthreads();
-        tc_stages<SchedT, S + 1, LAYOUT, T>(gin, gout, tile, stw, A, c, lane, ok, M, tc, tc_index + (I::tc ? 1 : 0));
+        tc_stages<SchedT, S + 1, LAYOUT, T, PREC>(gin, gout, tile, stw, A, c, lane, ok, M, tc, tc_index + (I::tc ? 1 : 0));
     }
 }
 
-// Shared memory: [twiddles: tw_pad float2][B operand: 4 KB][tile].  blockDim % 128 == 0.
-template <int LAYOUT, int N>
+// Shared memory: [twiddles: tw_pad float2][B operand: 4 KB][tile: the larger of the pass tile
+// and blockDim x 128 bytes (the A operands)].  blockDim % 128 == 0.
+template <int LAYOUT, int N, int PREC>
 __global__ void __launch_bounds__(512) croft_pass_kernel_tc(const float2* in, float2* out,
                                                              const __grid_constant__ PassArgs A) {
     using SchedT = Tc16Sched<N>;
@@ -303,7 +356,7 @@ __global__ void __launch_bounds__(512) croft_pass_kernel_tc(const float2* in, fl
         const long long m = cc - b * M;
         base = b * (long long)N * M + m;
     }
-    tc_stages<SchedT, 0, LAYOUT, T>(in + base, out + base, tile, stw, A, c, lane, ok, M, tc, 0);
+    tc_stages<SchedT, 0, LAYOUT, T, PREC>(in + base, out + base, tile, stw, A, c, lane, ok, M, tc, 0);
 
     asm volatile("tcgen05.fence::before_thread_sync;");
     __syncthreads();

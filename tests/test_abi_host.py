@@ -122,3 +122,26 @@ def test_row_layout_generator_models_the_library_schedule(croft_lib):
     for n in range(2, 4097):
         if gen.supported(n):
             assert gen.sched(n) == croft_lib.croft_factorize(n), n
+
+
+def test_noalloc_binding_rejects_bad_lists_before_the_library(croft_lib):
+    """The C side of croft_exec_batched_noalloc trusts dims for every size; the binding checks
+    the lists first: counts, element counts and dtype (CPU tensors, so nothing reaches a device)."""
+    import torch
+    dims = [(4, 4, 4), (2, 3, 5)]
+    good = [torch.zeros(d, dtype=torch.complex64) for d in dims]
+    with pytest.raises(ValueError, match="inputs and outputs"):
+        croft_lib.croft_exec_batched_noalloc_status(dims, good[:1], good, -1)
+    with pytest.raises(ValueError, match="inputs and outputs"):
+        croft_lib.croft_exec_batched_noalloc_status(dims, good, good[:1], -1)
+    short = [torch.zeros((4, 4, 3), dtype=torch.complex64), good[1]]
+    with pytest.raises(ValueError, match="elements"):
+        croft_lib.croft_exec_batched_noalloc_status(dims, short, good, -1)
+    wide = [torch.zeros(d, dtype=torch.complex128) for d in dims]
+    with pytest.raises(ValueError, match="complex64"):
+        croft_lib.croft_exec_batched_noalloc_status(dims, good, wide, -1)
+    with pytest.raises(ValueError, match="three axis lengths"):
+        croft_lib.croft_exec_batched_noalloc_status([(4, 4)], good[:1], good[:1], -1)
+    # well-formed lists get as far as the device check
+    with pytest.raises(ValueError, match="CUDA device"):
+        croft_lib.croft_exec_batched_noalloc_status(dims, good, good, -1)

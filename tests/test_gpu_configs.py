@@ -22,6 +22,44 @@ def tol(shape):
     return 2e-6 * math.log2(int(np.prod(shape)))
 
 
+def local_error_checks(y, ref, t):
+    """Checks that a localised mistake (one wrong tile, a wrong high-frequency block) cannot hide
+    under the whole-array rel L2 of a steeply decaying PME spectrum:
+
+    * per element: max |Y - Y_ref| / max |Y_ref| <= t;
+    * no outliers: max |Y - Y_ref| <= 40 x the rms error.  Rounding spreads error over every
+      output (the largest of N roughly Gaussian errors is ~6 rms at N = 1e8), while one wrong
+      tile of T elements puts its whole error there (max ~ sqrt(N / T) rms);
+    * the outer half of the spectrum (normalised |k| = sqrt(sum_a (m_a / (K_a / 2))^2) >= 1,
+      m_a the signed frequency): its error norm stays within its share of the error budget,
+      ||Y - Y_ref||_band <= 2 t ||Y_ref|| sqrt(N_band / N).
+    Returns (max_rel, outlier_ratio, band_rel)."""
+    nx, ny, nz = ref.shape
+    err2 = np.zeros(ref.shape, dtype=np.float64)
+    for x0 in range(0, nx, 32):
+        d = y[x0:x0 + 32].astype(np.complex128) - ref[x0:x0 + 32]
+        err2[x0:x0 + 32] = d.real ** 2 + d.imag ** 2
+    ref_abs_max = float(np.sqrt(max(float((r.real ** 2 + r.imag ** 2).max()) for r in ref)))
+    ref_norm = float(np.sqrt(sum(float((r.real ** 2 + r.imag ** 2).sum()) for r in ref)))
+    max_err = float(np.sqrt(err2.max()))
+    rms_err = float(np.sqrt(err2.mean()))
+
+    def f2(k):
+        m = np.arange(k, dtype=np.float64)
+        m = np.where(m <= k // 2, m, m - k)
+        return (m / (k / 2.0)) ** 2
+
+    band = (f2(nx)[:, None, None] + f2(ny)[None, :, None] + f2(nz)[None, None, :]) >= 1.0
+    band_err = float(np.sqrt(err2[band].sum()))
+    band_bar = 2.0 * t * ref_norm * math.sqrt(band.sum() / band.size)
+    max_rel = max_err / ref_abs_max
+    outlier = max_err / rms_err if rms_err > 0 else 0.0
+    assert max_rel <= t, ("per-element error", max_rel, t)
+    assert outlier <= 40.0, ("localised error", outlier)
+    assert band_err <= band_bar, ("high-|k| band error", band_err, band_bar)
+    return max_rel, outlier, band_err / band_bar
+
+
 def _check_grid(croft, x):
     shape = x.shape
     t = tol(shape)
@@ -32,6 +70,7 @@ def _check_grid(croft, x):
         yf_h = yf.cpu().numpy()
         ref_f = oracle.forward(x)
         ef = oracle.rel_l2(yf_h, ref_f)
+        loc = local_error_checks(yf_h, ref_f, t)
         ref_f32 = np.ascontiguousarray(ref_f, dtype=np.complex64)
         yb = p.backward(torch.from_numpy(ref_f32).cuda())
         torch.cuda.synchronize()
@@ -45,7 +84,8 @@ def _check_grid(croft, x):
     herm = np.linalg.norm(yf_h[np.ix_(*idx)] - np.conj(yf_h)) / np.linalg.norm(yf_h)
     dc_ref = complex(np.sum(x.astype(np.complex128)))
     scale = np.linalg.norm(yf_h) / math.sqrt(yf_h.size)
-    print(f"{shape}: rel_l2 fwd {ef:.3e} bwd {eb:.3e} roundtrip {er:.3e} hermitian {herm:.2e} (tol {t:.2e})")
+    print(f"{shape}: rel_l2 fwd {ef:.3e} bwd {eb:.3e} roundtrip {er:.3e} hermitian {herm:.2e} (tol {t:.2e}); "
+          f"max-elem {loc[0]:.2e}, max/rms {loc[1]:.1f}, band {loc[2]:.2f} of its bar")
     assert ef <= t and eb <= t and er <= t
     assert herm <= t
     assert abs(yf_h[0, 0, 0] - dc_ref) <= 1e-5 * scale * math.sqrt(x.size)

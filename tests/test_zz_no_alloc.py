@@ -12,6 +12,7 @@ import math
 import numpy as np
 import pytest
 
+import oracle
 import synthetic_inputs as S
 
 pytestmark = pytest.mark.gpu
@@ -22,6 +23,10 @@ DIMS = [(48, 60, 64), (8, 6, 4), (1, 1, 1), (128, 2, 3), (30, 1, 25), (72, 80, 9
 
 def _tol(shape):
     return 2e-6 * max(1.0, math.log2(int(np.prod(shape))))
+
+
+def _same_bits(a, b):
+    return torch.equal(a.view(torch.float32).view(torch.int32), b.view(torch.float32).view(torch.int32))
 
 
 def _rel(a, b):
@@ -49,8 +54,14 @@ def test_noalloc_matches_plan_based_batched_exec_twice(croft_lib):
         croft.croft_exec_batched_noalloc(DIMS, xs, outs_b, +1)
         torch.cuda.synchronize()
         for d, a, b, c, e in zip(DIMS, outs_f, ref_f, outs_b, ref_b):
-            assert _rel(a, b) <= _tol(d), (call, d, "forward")
-            assert _rel(c, e) <= _tol(d), (call, d, "backward")
+            # same kernel, same tiles, same arithmetic: the same bits as the plan-based call
+            assert _same_bits(a, b), (call, d, "forward", _rel(a, b))
+            assert _same_bits(c, e), (call, d, "backward", _rel(c, e))
+    # and against the FP64 oracle directly
+    for d, x, a, c in zip(DIMS, xs, outs_f, outs_b):
+        xh = x.cpu().numpy()
+        assert oracle.rel_l2(a.cpu().numpy(), oracle.forward(xh)) <= _tol(d), (d, "forward vs oracle")
+        assert oracle.rel_l2(c.cpu().numpy(), oracle.backward(xh)) <= _tol(d), (d, "backward vs oracle")
 
 
 def test_noalloc_pme_grids_and_limits(croft_lib):
@@ -65,12 +76,36 @@ def test_noalloc_pme_grids_and_limits(croft_lib):
     croft.croft_exec_batched_noalloc(dims, xs, outs, -1)
     torch.cuda.synchronize()
     for d, a, b in zip(dims, outs, ref):
-        assert _rel(a, b) <= _tol(d)
-    # beyond the static capacity: rejected before any device work
+        assert _same_bits(a, b), (d, _rel(a, b))
+    # beyond the static capacity: rejected by the library before any device work (raw addresses,
+    # which the binding passes through unchecked, reach the C-side checks)
+    p0 = xs[0].data_ptr()
     too_many = [(2, 2, 2)] * (croft.CROFT_NOALLOC_MAX_GRIDS + 1)
-    st = croft.croft_exec_batched_noalloc_status(too_many, [xs[0]] * len(too_many), [xs[0]] * len(too_many), -1)
+    st = croft.croft_exec_batched_noalloc_status(too_many, [p0] * len(too_many), [p0] * len(too_many), -1)
     assert st == croft.CROFT_ERR_UNSUPPORTED_SIZE
-    st = croft.croft_exec_batched_noalloc_status([(256, 4, 4)], [xs[0]], [xs[0]], -1)
+    st = croft.croft_exec_batched_noalloc_status([(256, 4, 4)], [p0], [p0], -1)
     assert st == croft.CROFT_ERR_UNSUPPORTED_SIZE
-    st = croft.croft_exec_batched_noalloc_status([(4, 4, 4)], [xs[0]], [xs[0]], 0)
+    st = croft.croft_exec_batched_noalloc_status([(4, 4, 4)], [p0], [p0], 0)
     assert st == croft.CROFT_ERR_INVALID_ARG
+
+
+def test_noalloc_refuses_a_capturing_stream(croft_lib):
+    """Its host tables live only for the call, so a copy recorded into a graph would read freed
+    memory on replay: the call returns CROFT_ERR_INVALID_ARG while the stream captures, before
+    any device work."""
+    from paper_2002_04896_gb300 import croft
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    dims = [(8, 6, 4)]
+    x = torch.zeros(dims[0], dtype=torch.complex64, device="cuda")
+    y = torch.empty_like(x)
+    croft.croft_exec_batched_noalloc(dims, [x], [y], -1)  # first call on the device: set-up outside capture
+    torch.cuda.synchronize()
+    s = torch.cuda.Stream()
+    g = torch.cuda.CUDAGraph()
+    statuses = []
+    with torch.cuda.stream(s):
+        with torch.cuda.graph(g, stream=s):
+            statuses.append(croft.croft_exec_batched_noalloc_status(dims, [x], [y], -1, s))
+            y.add_(0)  # one captured op, so the graph is not empty
+    assert statuses == [croft.CROFT_ERR_INVALID_ARG]
