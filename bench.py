@@ -18,8 +18,9 @@ events over K more steps run right after the timed ones.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl croft|reference]
 
-With N > 1 (torchrun) every rank runs an independent replica of the workload
-and value is the sum over ranks; the time is the max over ranks.
+With N > 1 (torchrun) the one grid is split over the ranks in x-slabs (the paper's
+slab decomposition: local z and y passes, one NCCL all-to-all, local x pass) and value
+is the job's throughput on that grid (strong scaling); the time is the max over ranks.
 
 --impl reference times the FP64 CPU oracle (the only reference this method has)
 on the host cores, on a bounded sample of the same workload.
@@ -656,6 +657,168 @@ class Arm:
         return [statistics.mean([r[0][i] for r in self.rec_pp] + [r[1][i] for r in self.rec_pp]) for i in range(npass)]
 
 
+def run_slab(args, world, rank, local):  # noqa: PLR0915
+    """N > 1: the one pme512 transform split over the ranks in x-slabs (paper Sec. 2.2.1): z and y
+    passes on each rank's slab, one NCCL all-to-all, the x pass on its y-slab; backward the other
+    way round (paper_2002_04896_gb300.slab).  Strong scaling: the job transforms one grid per step."""
+    import numpy as np
+    import torch
+    import torch.distributed as dist
+
+    import synthetic_inputs as S
+    from paper_2002_04896_gb300 import build as _build
+
+    _build.ensure_built()
+    from paper_2002_04896_gb300 import croft, slab
+
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    dist.init_process_group("nccl", device_id=dev)
+    t_in = time.perf_counter()
+    x_h = S.config_input(CONFIG)  # every rank draws the same grid (seeded) and keeps its slab
+    t_in = time.perf_counter() - t_in
+    shape = x_h.shape
+    n_total = math.prod(shape)
+    flops_step = 2 * nominal_flops(shape)
+    fft = slab.SlabFFT(shape)
+    nxl = fft.shape_x[0]
+    x_slab = np.ascontiguousarray(x_h[rank * nxl:(rank + 1) * nxl])
+    del x_h
+    xs = torch.from_numpy(x_slab).to(dev)
+    work = torch.empty_like(xs)
+    back = torch.empty_like(xs)
+    ys = torch.empty(fft.shape_y, dtype=torch.complex64, device=dev)
+    ywork = torch.empty_like(ys)
+    flush = torch.empty((1 << 30) // 4, dtype=torch.float32, device=dev)
+    ops = fft.ops
+
+    def step(record=None, fills=1):
+        for _ in range(fills):
+            flush.fill_(1.0)
+        e = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
+        e[0].record()
+        fft.forward(xs, ys, work=work)
+        fft.backward(ys, back, work=ywork)
+        e[1].record()
+        torch.cuda.synchronize()
+        if record is not None:
+            record.append(e[0].elapsed_time(e[1]))
+
+    for _ in range(args.warmup):
+        step()
+    a = torch.cuda.Event(enable_timing=True)
+    b = torch.cuda.Event(enable_timing=True)
+    a.record()
+    for _ in range(10):
+        flush.fill_(1.0)
+    b.record()
+    torch.cuda.synchronize()
+    fills = max(1, int(math.ceil(args.clock_window_s / max(1, args.steps) / (a.elapsed_time(b) / 10 * 1e-3))))
+    clocks = ClockSampler(torch.cuda.current_device()) if rank == 0 else None
+    if clocks:
+        clocks.start()
+    dist.barrier()
+    torch.cuda.synchronize()
+    rec = []
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        step(rec, fills)
+    torch.cuda.synchronize()
+    t_wall = time.perf_counter() - t0
+    dist.barrier()
+    # stage times (events between the stages) and per-pass times of the local plans
+    croft.croft_plan_set_timing(ops.plan_x.handle, True)
+    croft.croft_plan_set_timing(ops.plan_y.handle, True)
+    stages, passes = [], []
+    for _ in range(args.steps):
+        flush.fill_(1.0)
+        ev = [torch.cuda.Event(enable_timing=True) for _ in range(7)]
+        ev[0].record()
+        send = fft.forward_send(xs, work=work)
+        ev[1].record()
+        pz = croft.croft_plan_pass_times(ops.plan_x.handle)
+        recv = fft.buffers(xs)[1]
+        fft.exchange(send, recv)
+        ev[2].record()
+        fft.forward_finish(recv, ys)
+        ev[3].record()
+        px = croft.croft_plan_pass_times(ops.plan_y.handle)
+        send = fft.backward_send(ys, work=ywork)
+        ev[4].record()
+        fft.exchange(send, recv)
+        ev[5].record()
+        fft.backward_finish(recv, back)
+        ev[6].record()
+        torch.cuda.synchronize()
+        stages.append([ev[i].elapsed_time(ev[i + 1]) for i in range(6)])
+        passes.append(pz + px)
+    croft.croft_plan_set_timing(ops.plan_x.handle, False)
+    croft.croft_plan_set_timing(ops.plan_y.handle, False)
+    clk = clocks.stop() if clocks else None
+    ms_step = max_over_ranks(torch, sum(rec) / args.steps, dev)
+    value = flops_step / (ms_step * 1e-3) / 1e9
+    st = [statistics.mean(v[i] for v in stages) for i in range(6)]
+    pass_ms = [statistics.mean(v[i] for v in passes) for i in range(len(passes[0]))]
+    # round trip on every rank, reduced over the job
+    d = (back - n_total * xs).flatten()
+    red = torch.tensor([float(torch.linalg.vector_norm(d)) ** 2,
+                        float(torch.linalg.vector_norm(n_total * xs.flatten())) ** 2], dtype=torch.float64, device=dev)
+    dist.all_reduce(red)
+    rt = math.sqrt(float(red[0]) / float(red[1]))
+    peak, peak_kind = measured_peaks()
+    local_bytes = 16.0 * n_total / world
+    dom = max(range(len(pass_ms)), key=lambda i: pass_ms[i])
+    achieved = local_bytes / (pass_ms[dom] * 1e-3) / 1e9
+    # end to end: every step uploads each rank's slab from pinned memory and downloads its result
+    x_pin = torch.from_numpy(x_slab).pin_memory()
+    b_pin = torch.empty_like(x_pin).pin_memory()
+    e2e_rec = []
+    for i in range(args.warmup + args.steps):
+        e = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
+        e[0].record()
+        xs.copy_(x_pin, non_blocking=True)
+        fft.forward(xs, ys, work=work)
+        fft.backward(ys, back, work=ywork)
+        b_pin.copy_(back, non_blocking=True)
+        e[1].record()
+        torch.cuda.synchronize()
+        if i >= args.warmup:
+            e2e_rec.append(e[0].elapsed_time(e[1]))
+    e2e_ms = max_over_ranks(torch, statistics.mean(e2e_rec), dev)
+    launches = args.steps * 2 * (croft.croft_plan_num_launches(ops.plan_x.handle) +
+                                 croft.croft_plan_num_launches(ops.plan_y.handle))
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": "GFLOP/s", "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "strong",
+            "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": WORKLOAD.split(";")[0] + "; FP32 path, one grid split over the GPUs in x-slabs",
+                       "grid": list(shape), "direction": "forward+backward",
+                       "parallelism": f"slab x{world}: z+y passes per x-slab, one all-to-all, x pass per y-slab",
+                       "l2": "L2 flushed before every step (1 GiB write, outside the timed events)",
+                       "input_generation_s": t_in},
+            "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+                         "traffic": None, "kernel": ["z", "y", "x"][dom] + f" pass of a {world}-way slab",
+                         "peak_source": peak_kind, "alg_bytes_per_launch": local_bytes, "pass_ms": pass_ms,
+                         "kernel_timing": "per-pass CUDA events of the local plans, rank 0"},
+            "slab": {"stage_ms_rank0": dict(zip(["fwd_local_zy+pack", "fwd_all_to_all", "fwd_local_x",
+                                                 "bwd_local_x", "bwd_all_to_all", "bwd_unpack+local_zy"], st)),
+                     "exchange_bytes_per_rank_per_all_to_all": 8 * fft.block * (world - 1)},
+            "errors": {"rel_l2_roundtrip": rt, "bar_rel_l2": FP32_TOL_PER_LOG2 * math.log2(n_total)},
+            "tc": None, "cpu_baseline": None,
+            "e2e": {"value": flops_step / (e2e_ms * 1e-3) / 1e9, "unit": "GFLOP/s", "h2d_bytes_per_step": 8 * n_total,
+                    "d2h_bytes_per_step": 8 * n_total, "ms_per_step": e2e_ms,
+                    "api": "SlabFFT.forward/backward per step, each rank's slab copied from and to pinned memory"},
+            "gpu_launches": launches,
+            "gpu_launches_note": "croft kernels of rank 0 inside its timed steps (NCCL and copy-engine copies not counted)",
+            "clocks": clk, "wall_s_timed_region": t_wall,
+        }
+        print(json.dumps(line), flush=True)
+    fft.close()
+    dist.destroy_process_group()
+    return 0
+
+
 def run_croft(args):  # noqa: PLR0915
     import numpy as np
     import torch
@@ -668,8 +831,7 @@ def run_croft(args):  # noqa: PLR0915
 
     world, rank, local = dist_env()
     if world > 1:
-        import torch.distributed as dist
-        dist.init_process_group("nccl")
+        return run_slab(args, world, rank, local)
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
 

@@ -289,7 +289,8 @@ croft_status croft_exec_backward(croft_plan plan, const void* in, void* out, voi
  *   axes      : bit a set to transform axis a (0 = x, 1 = y, 2 = z); 0 copies in to out.
  *   direction : -1 forward (Eq. 1), +1 backward (Eq. 2, unnormalised).
  *   stream    : cudaStream_t or NULL.
- * Returns CROFT_OK, CROFT_ERR_INVALID_ARG or CROFT_ERR_CUDA.  Asynchronous like exec.
+ * Returns CROFT_OK, CROFT_ERR_INVALID_ARG or CROFT_ERR_CUDA.  Asynchronous like exec; with
+ * croft_plan_set_timing enabled it records one event per pass it runs (croft_plan_pass_times).
  */
 croft_status croft_exec_axes(croft_plan plan, const void* in, void* out, int axes, int direction, void* stream);
 

@@ -730,6 +730,12 @@ croft_status croft_exec_axes(croft_plan plan, const void* in, void* out, int axe
         return CROFT_ERR_CUDA;
     }
     const float isign = direction == -1 ? 1.0f : -1.0f;
+    const bool tm = plan->timing;  // per-pass events as for exec (croft_plan_pass_times)
+    int evi = 0;
+    if (tm) {
+        if (cudaEventRecord(plan->ev[0], s) != cudaSuccess) { cudaGetLastError(); return CROFT_ERR_CUDA; }
+        evi = 1;
+    }
     bool started = false, first = true;
     for (size_t i = 0; i < plan->passes.size(); ++i) {
         if (!(axes & (1 << plan->pass_axis[i]))) continue;
@@ -742,13 +748,17 @@ croft_status croft_exec_axes(croft_plan plan, const void* in, void* out, int axe
             return CROFT_ERR_CUDA;
         }
         first = false;
+        if (tm && cudaEventRecord(plan->ev[evi++], s) != cudaSuccess) {
+            cudaGetLastError();
+            return CROFT_ERR_CUDA;
+        }
     }
     // no pass ran (no selected axis longer than 1): the selected transforms are the identity
     if (first && in != out && cudaMemcpyAsync(out, in, bytes, cudaMemcpyDeviceToDevice, s) != cudaSuccess) {
         cudaGetLastError();
         return CROFT_ERR_CUDA;
     }
-    plan->ev_count = 0;
+    plan->ev_count = tm ? evi : 0;
     plan->ran = true;
     return CROFT_OK;
 }

@@ -25,14 +25,15 @@
 // Hardware path (sm_103a): operands in shared memory in the K-major,
 // no-swizzle core-matrix layout (8 rows x 16 bytes per core matrix; core
 // matrices adjacent in K are 128 B apart, row groups 512 B apart); one thread
-// issues tcgen05.mma.cta_group::1.kind::f16 (bf16 in, f32 accumulate) for
-// every 128-row group into its own 32 TMEM columns, commits to an mbarrier,
-// and every warp reads its 32 rows back with tcgen05.ld.32x32b.x32: thread t
+// issues tcgen05.mma.cta_group::1.kind::f16 (bf16 or fp16 in, f32 accumulate)
+// for every 128-row group into its own 32 TMEM columns and commits to an
+// mbarrier; one warp waits for it while the others wait at the CTA barrier, and
+// every warp then reads its 32 rows back with tcgen05.ld.32x32b.x32: thread t
 // receives the 32 accumulators of butterfly t.  The twiddles, the hi/lo split
 // and the other radices stay on the CUDA cores.
 //
 // The operand buffers (A hi + A lo, 128 bytes per butterfly) reuse the pass's
-// shared-memory tile, which is exactly 128 bytes per thread: every input of
+// shared-memory tile, sized to at least 128 bytes per thread: every input of
 // the stage is in registers before the tile is overwritten, and every MMA has
 // completed (mbarrier) before the outputs are written back into it.
 #pragma once
@@ -212,7 +213,10 @@ __device__ __forceinline__ void fft_stage_tc16(const Src& src, const Dst& dst, c
         }
         asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(tc.mbar));
     }
-    if (!tc_wait(tc.mbar, parity) && tc.status) atomicExch(tc.status, 5 /* CROFT_ERR_TIMEOUT */);
+    // one warp waits for the MMAs' commit (bounded), the others at the CTA barrier (no polling);
+    // the barrier then orders every thread's TMEM reads after the completed MMAs
+    if (tid < 32 && !tc_wait(tc.mbar, parity) && tc.status && tid == 0) atomicExch(tc.status, 5 /* CROFT_ERR_TIMEOUT */);
+    __syncthreads();
     asm volatile("tcgen05.fence::after_thread_sync;");
     float d[32];
     const int warp = tid >> 5;
