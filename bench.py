@@ -375,7 +375,7 @@ def errors_vs_oracle(x_h, y_h, z_h, ref, slab: int = 32):
             "rel_l2_roundtrip": q(acc["rnum"], acc["rden"])}
 
 
-ROW_NAMES = ("pme256_fp32", "pme480_fp32", "pme384x360x320_fp32", "pme256_convolve", "f64_128", "f64_1024",
+ROW_NAMES = ("pme256_fp32", "pme480_fp32", "pme384x360x320_fp32", "tuned", "pme256_convolve", "f64_128", "f64_1024",
              "batch96")
 
 
@@ -429,6 +429,40 @@ def measure_rows(croft, torch, dev, stream, flush, peak, peak_kind, only=None): 
                       "roundtrip_rel_l2": rt, "plan": desc, "cufft_torch_fftn_context": cufft,
                       "input": "pme256 (seed 1, 200k charges)" if name == "pme256_fp32" else "device uniform noise"}
         del x, y
+    if want("tuned"):
+        # CROFT_SCHEDULE_TUNED (measured at plan creation, fresh cache) against the rules (AUTO)
+        import tempfile
+        trow = {}
+        with tempfile.TemporaryDirectory() as td:
+            old_cache = os.environ.get("CROFT_TUNE_CACHE")
+            os.environ["CROFT_TUNE_CACHE"] = os.path.join(td, "tune.txt")
+            try:
+                for shape in ((512, 512, 512), (480, 480, 480), (384, 360, 320)):
+                    x = grid(shape)
+                    y = torch.empty_like(x)
+                    z = torch.empty_like(x)
+                    sh = stream.cuda_stream
+                    res = {}
+                    for name, sched in (("rules", None), ("tuned", croft.CROFT_SCHEDULE_TUNED)):
+                        t0 = time.perf_counter()
+                        with croft.Plan(*shape, schedule=sched) as p:
+                            t_plan = time.perf_counter() - t0
+                            f_ms, b_ms, _ = time_transform(
+                                croft, torch, stream, flush, None,
+                                lambda: croft.croft_exec_forward(p.handle, x, y, sh),
+                                lambda: croft.croft_exec_backward(p.handle, y, z, sh), reps=10, warm=3)
+                            desc = p.describe()
+                        res[name] = {"ms": f_ms + b_ms, "plan_creation_s": t_plan,
+                                     "choice": desc.split("| tuned")[-1].strip() if name == "tuned" else "rules"}
+                    res["speedup_tuned_vs_rules"] = res["rules"]["ms"] / res["tuned"]["ms"]
+                    trow["x".join(map(str, shape))] = res
+                    del x, y, z
+            finally:
+                if old_cache is None:
+                    os.environ.pop("CROFT_TUNE_CACHE", None)
+                else:
+                    os.environ["CROFT_TUNE_CACHE"] = old_cache
+        rows["tuned"] = trow
     if want("pme256_convolve"):
         # PME reciprocal-space convolution B(G * F(x)) on 256^3 with the smooth-PME influence function:
         # croft_exec_convolve (last-axis forward * G * backward fused) vs forward, a torch multiply, backward

@@ -111,12 +111,22 @@ croft_status croft_plan_create(croft_plan* out, int nx, int ny, int nz, croft_dt
  *       the transposes into K pieces (Sec. 5.1), here sized to the cache.
  *   CROFT_SCHEDULE_AUTO : THREE_PASS (measured faster on GB300 so far); with the
  *       environment variable CROFT_SCHEDULE_AUTO_FUSED=1, PLANE_FUSED where available.
+ *   CROFT_SCHEDULE_TUNED : measured at plan creation (the paper tunes its options 1-4 and
+ *       the chunk count K by hand, Sec. 5.1): for each column pass of a 270..512-point axis
+ *       the kernel (16- or 8-column tile, near-equal or radix-16-first power-of-two split,
+ *       or the tensor-copy ring kernel), then the schedule (three-pass with those kernels,
+ *       slab, fused plane), each timed on the device; the fastest is kept and cached on
+ *       disk (CROFT_TUNE_CACHE, default ~/.croft_tune_cache.txt) keyed by shape, dtype, GPU
+ *       and CUDA version.  Needs two grid-sized scratch buffers during creation (without
+ *       them it plans by the rules); croft_plan_describe reports the choice.  Tensor-core
+ *       and complex128 plans have nothing to choose and plan THREE_PASS.
  */
 typedef enum {
     CROFT_SCHEDULE_AUTO = 0,
     CROFT_SCHEDULE_THREE_PASS = 1,
     CROFT_SCHEDULE_PLANE_FUSED = 2,
-    CROFT_SCHEDULE_SLAB_L2 = 3
+    CROFT_SCHEDULE_SLAB_L2 = 3,
+    CROFT_SCHEDULE_TUNED = 4
 } croft_schedule;
 
 /*

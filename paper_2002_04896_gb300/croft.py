@@ -26,6 +26,7 @@ CROFT_SCHEDULE_AUTO = 0
 CROFT_SCHEDULE_THREE_PASS = 1
 CROFT_SCHEDULE_PLANE_FUSED = 2
 CROFT_SCHEDULE_SLAB_L2 = 3
+CROFT_SCHEDULE_TUNED = 4
 
 CROFT_NOALLOC_MAX_GRIDS = 256
 CROFT_NOALLOC_MAX_ITEMS = 65536

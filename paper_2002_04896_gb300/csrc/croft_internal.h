@@ -78,6 +78,7 @@ struct PassLaunch {
     int layout;
     int tc;             // tensor-core variant of the pass kernel: 0 none, 1 + operand precision (TcPrec)
     int f64;            // 1: complex128 pass kernel
+    int sv;             // schedule variant of a plain pass kernel (croft_pass_sched_v)
     int ring;           // 1: tensor-copy ring kernel (RingArgs below)
     RingArgs ra;
     long long B;        // ring: outer extent of the tensor map (batch rows)
@@ -94,11 +95,12 @@ const PlaneKernel* find_plane_kernel(int ny, int nz, int cluster);
 // croft_ring.cu: the tensor-copy ring column kernel (NULL if not instantiated for n)
 ring_fn ring_kernel_for(int n);
 
-// croft_kernels.cu, one per size group (w: the COL tile width; ignored for ROW)
-pass_fn lookup_pass_kernel_group_0(int layout, int n, int w);
-pass_fn lookup_pass_kernel_group_1(int layout, int n, int w);
-pass_fn lookup_pass_kernel_group_2(int layout, int n, int w);
-pass_fn lookup_pass_kernel_group_3(int layout, int n, int w);
+// croft_kernels.cu, one per size group (w: the COL tile width, ignored for ROW; sv: the
+// schedule variant, croft_pass_sched_v)
+pass_fn lookup_pass_kernel_group_0(int layout, int n, int w, int sv);
+pass_fn lookup_pass_kernel_group_1(int layout, int n, int w, int sv);
+pass_fn lookup_pass_kernel_group_2(int layout, int n, int w, int sv);
+pass_fn lookup_pass_kernel_group_3(int layout, int n, int w, int sv);
 
 // croft_tc.cu: tensor-core pass kernels (NULL when n has no instantiation); prec 0 = split
 // bf16, 1 = split fp16 with per-butterfly power-of-two scaling (TcPrec)
@@ -129,8 +131,8 @@ cudaError_t launch_scale(const void* in, void* out, const void* g, long long n, 
 extern int g_max_smem;  // the device's opt-in shared memory per block (set by plan creation)
 // Launch shape of one axis pass (tile width, block, grid, shared memory); false when no shape fits.
 bool shape_pass(PassLaunch& L, int layout, int n, long long M, long long ncols, int tc = 0, bool f64 = false,
-                int want_w = 0);
-pass_fn pass_kernel_for(int layout, int n, int w);
+                int want_w = 0, int sv = 0);
+pass_fn pass_kernel_for(int layout, int n, int w, int sv = 0);
 conv_fn conv_kernel_for(int n);
 // Launch shape of a ring column pass (one persistent CTA per SM); false when the pass does not
 // qualify (length, odd stride, shared memory).

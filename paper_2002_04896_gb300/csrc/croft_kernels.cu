@@ -13,16 +13,21 @@
 namespace croft {
 
 // One COL kernel per length: tile width croft_col_width, launch bound croft_col_minb;
-// lengths of 32-thread pencils add the narrow short-stride kernel (croft_col_width_at).
+// lengths of 32-thread pencils add the narrow short-stride kernel (croft_col_width_at) and,
+// for tuned plans, both widths with the other schedule variant (sv = 1).
 // w: the width asked for (nullptr when no kernel is built for it).
 template <int N>
-static pass_fn col_kernel(int w) {
+static pass_fn col_kernel(int w, int sv) {
     constexpr int W = croft_col_width(N, 8);
-    if constexpr (croft_threads_per_pencil(N) == 32 && W != kColNarrowWidth)
+    if constexpr (croft_threads_per_pencil(N) == 32 && W != kColNarrowWidth) {
         if (w == kColNarrowWidth)
-            return croft_pass_kernel_bounded<LAYOUT_COL, N, float2, kColNarrowWidth, croft_col_narrow_minb(N),
-                                             kColNarrowWidth * 32>;
-    if (w != W) return nullptr;
+            return sv ? croft_pass_kernel_bounded<LAYOUT_COL, N, float2, kColNarrowWidth, croft_col_narrow_minb(N),
+                                                  kColNarrowWidth * 32, 1>
+                      : croft_pass_kernel_bounded<LAYOUT_COL, N, float2, kColNarrowWidth, croft_col_narrow_minb(N),
+                                                  kColNarrowWidth * 32>;
+        if (w == W && sv) return croft_pass_kernel_bounded<LAYOUT_COL, N, float2, W, croft_col_minb(N, 8), 512, 1>;
+    }
+    if (w != W || sv) return nullptr;
     if constexpr (croft_col_minb(N, 8) > 1) return croft_pass_kernel_bounded<LAYOUT_COL, N, float2, W, croft_col_minb(N, 8)>;
     else if constexpr (croft_pass_minb(N, 8) > 0)
         return croft_pass_kernel_bounded<LAYOUT_COL, N, float2, W, croft_pass_minb(N, 8), 256>;
@@ -35,9 +40,9 @@ static pass_fn row_kernel() {
     else return croft_pass_kernel<LAYOUT_ROW, N>;
 }
 
-pass_fn CROFT_CAT(lookup_pass_kernel_group_, CROFT_GROUP)(int layout, int n, int w) {
+pass_fn CROFT_CAT(lookup_pass_kernel_group_, CROFT_GROUP)(int layout, int n, int w, int sv) {
 #define CROFT_CASE(N) \
-    case N: return layout == LAYOUT_ROW ? row_kernel<N>() : col_kernel<N>(w);
+    case N: return layout == LAYOUT_ROW ? (sv ? nullptr : row_kernel<N>()) : col_kernel<N>(w, sv);
     switch (n) {
         CROFT_CAT(CROFT_SIZES_, CROFT_GROUP)(CROFT_CASE)
         default: return nullptr;

@@ -29,7 +29,7 @@ namespace croft {
 // (complex64, the default) or double2 (complex128, twiddles from A.tw64).
 // COL kernels are specialised on the column-tile width WC as well (so the
 // shared-memory indices fold into constants); ROW kernels take W from A.W.
-template <int LAYOUT, int N, class C, int WC>
+template <int LAYOUT, int N, class C, int WC, int SV = 0>
 __device__ __forceinline__ void pass_body(const C* in, C* out, const PassArgs& A) {
     constexpr int T = croft_threads_per_pencil(N);
     extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -64,7 +64,8 @@ __device__ __forceinline__ void pass_body(const C* in, C* out, const PassArgs& A
         const GlobalInT<C> src{in + base, A.M, A.isign};
         const SmemColFixed<C, (WC > 0 ? WC : 1)> work{sbuf + c};
         const GlobalOutT<C> dst{out + base, A.M, A.isign};
-        if constexpr (croft_even_pow2_pass(N, LAYOUT_COL, (int)sizeof(C)))
+        // the column schedule (croft_pass_sched_v: SV = 1 is the radix-16-first variant)
+        if constexpr (SV == 0 && croft_even_pow2_pass(N, LAYOUT_COL, (int)sizeof(C)))
             fft_pencil_s<EvenPow2Sched<N>, T>(src, work, dst, stw, lane, ok);
         else
             fft_pencil<N, T>(src, work, dst, stw, lane, ok);
@@ -80,11 +81,11 @@ __global__ void __launch_bounds__(512) croft_pass_kernel(const C* in, C* out, co
 }
 
 // The same with registers bounded for MINB CTAs of MAXT threads per SM (croft_col_minb,
-// croft_pass_minb).
-template <int LAYOUT, int N, class C, int WC, int MINB, int MAXT = 512>
+// croft_pass_minb); SV selects the schedule variant (croft_pass_sched_v).
+template <int LAYOUT, int N, class C, int WC, int MINB, int MAXT = 512, int SV = 0>
 __global__ void __launch_bounds__(MAXT, MINB) croft_pass_kernel_bounded(const C* in, C* out,
                                                                          const __grid_constant__ PassArgs A) {
-    pass_body<LAYOUT, N, C, WC>(in, out, A);
+    pass_body<LAYOUT, N, C, WC, SV>(in, out, A);
 }
 
 }  // namespace croft

@@ -17,10 +17,11 @@ int g_max_smem = 0;
 // COL: W adjacent columns per CTA, W a multiple of 16 (128-byte rows).
 // Aim for ~256 threads per CTA and <= 100 KB of shared memory so that at
 // least two CTAs share an SM.
-bool shape_pass(PassLaunch& L, int layout, int n, long long M, long long ncols, int tc, bool f64, int want_w) {
+bool shape_pass(PassLaunch& L, int layout, int n, long long M, long long ncols, int tc, bool f64, int want_w, int sv) {
     memset(&L, 0, sizeof(L));
     L.layout = layout;
     L.tc = tc;
+    L.sv = sv;
     L.f64 = f64 ? 1 : 0;
     const long long es = f64 ? 16 : 8;  // bytes per element
     PassArgs& A = L.args;
@@ -141,11 +142,11 @@ bool shape_ring(PassLaunch& L, int n, long long M, long long ncols) {
     return L.grid > 0 && tensor_map_encoder() != nullptr;
 }
 
-pass_fn pass_kernel_for(int layout, int n, int w) {
-    pass_fn f = lookup_pass_kernel_group_0(layout, n, w);
-    if (!f) f = lookup_pass_kernel_group_1(layout, n, w);
-    if (!f) f = lookup_pass_kernel_group_2(layout, n, w);
-    if (!f) f = lookup_pass_kernel_group_3(layout, n, w);
+pass_fn pass_kernel_for(int layout, int n, int w, int sv) {
+    pass_fn f = lookup_pass_kernel_group_0(layout, n, w, sv);
+    if (!f) f = lookup_pass_kernel_group_1(layout, n, w, sv);
+    if (!f) f = lookup_pass_kernel_group_2(layout, n, w, sv);
+    if (!f) f = lookup_pass_kernel_group_3(layout, n, w, sv);
     return f;
 }
 
@@ -227,7 +228,7 @@ cudaError_t prepare_pass(const PassLaunch& L) {
         if (L.smem <= 48 * 1024) return cudaSuccess;
         return cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, L.smem);
     }
-    pass_fn f = L.tc ? tc_pass_kernel_for(L.layout, L.args.n, L.tc - 1) : pass_kernel_for(L.layout, L.args.n, L.args.W);
+    pass_fn f = L.tc ? tc_pass_kernel_for(L.layout, L.args.n, L.tc - 1) : pass_kernel_for(L.layout, L.args.n, L.args.W, L.sv);
     if (!f) return cudaErrorInvalidValue;
     if (L.smem <= 48 * 1024) return cudaSuccess;
     return cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, L.smem);
@@ -265,7 +266,7 @@ cudaError_t launch_pass(const PassLaunch& L, const void* vin, void* vout, cudaSt
         f<<<L.grid, L.block, L.smem, s>>>(in, out, L.args);
         return cudaGetLastError();
     }
-    pass_fn f = pass_kernel_for(L.layout, L.args.n, L.args.W);
+    pass_fn f = pass_kernel_for(L.layout, L.args.n, L.args.W, L.sv);
     if (!f) return cudaErrorInvalidValue;
     return launch_ex(f, L, s, pdl, in, out, L.args);
 }

@@ -12,6 +12,7 @@
 #include <stdlib.h>
 #include <string.h>
 
+#include <algorithm>
 #include <new>
 #include <string>
 #include <vector>
@@ -177,12 +178,13 @@ static croft_status add_axis_pass(croft_plan p, int axis, int x0 = 0, int nxs = 
     const long long M = (axis == 2) ? 1 : (axis == 1 ? (long long)nz : (long long)ny * nz);
     const int layout = M == 1 ? LAYOUT_ROW : LAYOUT_COL;
     const bool f64 = p->dtype == CROFT_C2C_F64;
-    // Column passes of 32-thread pencils (270..512 points) whose axis elements lie more than
-    // 16 KB apart (the x pass) run the tensor-copy ring kernel; CROFT_RING=1 takes it for
-    // every such column pass, CROFT_RING=0 for none (both for measurement).
+    // The tensor-copy ring kernel serves column passes of 32-thread pencils when the rules
+    // (croft_ring_default) or a tuned plan pick it; CROFT_RING=1 takes it for every such column
+    // pass, CROFT_RING=0 for none (both for measurement).
+    const int kind = p->axis_kind[axis];
     const char* re = getenv("CROFT_RING");
     const bool ring_pass = layout == LAYOUT_COL && !f64 && !p->axis_tc[axis] &&
-                           (re ? re[0] == '1' : croft_ring_default(n, 8, M * 8));
+                           (kind >= 0 ? kind == 1 : (re ? re[0] == '1' : croft_ring_default(n, 8, M * 8)));
     if (ring_pass) {
         PassLaunch L;
         if (shape_ring(L, n, M, N / n)) {
@@ -201,7 +203,9 @@ static croft_status add_axis_pass(croft_plan p, int axis, int x0 = 0, int nxs = 
         }
     }
     PassLaunch L;
-    if (!shape_pass(L, layout, n, M, N / n, p->axis_tc[axis] ? 1 + p->tc_prec : 0, f64)) return CROFT_ERR_UNSUPPORTED_SIZE;
+    const int want_w = kind == 0 ? p->axis_w[axis] : 0, sv = kind == 0 ? p->axis_sv[axis] : 0;
+    if (!shape_pass(L, layout, n, M, N / n, p->axis_tc[axis] ? 1 + p->tc_prec : 0, f64, want_w, sv))
+        return CROFT_ERR_UNSUPPORTED_SIZE;
     L.kind = PASS_AXIS;
     L.args.tw = p->tw_dev[axis];
     L.args.tw64 = f64 ? (const double2*)p->tw_dev[axis] : nullptr;
@@ -279,7 +283,8 @@ static void plan_conv(croft_plan p) {
     const long long M = (axis == 2) ? 1 : (axis == 1 ? (long long)p->dims[2] : (long long)p->dims[1] * p->dims[2]);
     if (f64 ? !conv64_kernel_for(n) : !conv_kernel_for(n)) return;
     // the fused kernel runs the column schedule; the axis's twiddle table follows its pass's
-    const CroftSched sa = croft_pass_sched(n, Lp.layout, f64 ? 16 : 8), sb = croft_pass_sched(n, LAYOUT_COL, f64 ? 16 : 8);
+    const CroftSched sa = croft_pass_sched_v(n, Lp.layout, f64 ? 16 : 8, Lp.sv),
+                     sb = croft_pass_sched(n, LAYOUT_COL, f64 ? 16 : 8);
     if (sa.count != sb.count) return;
     for (int i = 0; i < sa.count; ++i)
         if (sa.r[i] != sb.r[i]) return;
@@ -312,7 +317,15 @@ static void plan_conv(croft_plan p) {
     p->conv_fused = true;
 }
 
-static croft_status create_impl(croft_plan* out, int nx, int ny, int nz, croft_dtype dtype, croft_schedule sched) {
+// Per-axis kernel choice of a tuned plan (croft_plan_s::axis_kind / axis_w / axis_sv).
+struct AxisChoice {
+    int kind[3] = {-1, -1, -1};
+    int w[3] = {0, 0, 0};
+    int sv[3] = {0, 0, 0};
+};
+
+static croft_status create_impl(croft_plan* out, int nx, int ny, int nz, croft_dtype dtype, croft_schedule sched,
+                                const AxisChoice* choice = nullptr) {
     if (!out) return CROFT_ERR_INVALID_ARG;
     *out = NULL;
     if (dtype != CROFT_C2C_F32 && dtype != CROFT_C2C_F32_TC_BF16X3 && dtype != CROFT_C2C_F32_TC_FP16X3 &&
@@ -326,7 +339,7 @@ static croft_status create_impl(croft_plan* out, int nx, int ny, int nz, croft_d
     }
     if (sched != CROFT_SCHEDULE_AUTO && sched != CROFT_SCHEDULE_THREE_PASS && sched != CROFT_SCHEDULE_PLANE_FUSED &&
         sched != CROFT_SCHEDULE_SLAB_L2)
-        return CROFT_ERR_INVALID_ARG;
+        return CROFT_ERR_INVALID_ARG;  // (CROFT_SCHEDULE_TUNED resolves to one of these first)
     if (!axis_supported(nx) || !axis_supported(ny) || !axis_supported(nz)) return CROFT_ERR_UNSUPPORTED_SIZE;
 
     int dev = 0;
@@ -354,6 +367,11 @@ static croft_status create_impl(croft_plan* out, int nx, int ny, int nz, croft_d
     p->d_status = NULL;
     p->conv_fused = false;
     p->conv_axis = -1;
+    for (int a = 0; a < 3; ++a) {
+        p->axis_kind[a] = choice ? choice->kind[a] : -1;
+        p->axis_w[a] = choice ? choice->w[a] : 0;
+        p->axis_sv[a] = choice ? choice->sv[a] : 0;
+    }
     const char* pdl_env = getenv("CROFT_PDL");  // 0: ordinary stream ordering between passes (for measurement)
     p->pdl = !(pdl_env && pdl_env[0] == '0');
     const bool want_tc = dtype == CROFT_C2C_F32_TC_BF16X3 || dtype == CROFT_C2C_F32_TC_FP16X3;
@@ -390,7 +408,8 @@ static croft_status create_impl(croft_plan* out, int nx, int ny, int nz, croft_d
         } else {
             // the schedule of the axis's pass (a unit element stride makes it a row pass)
             const long long M = (axis == 2) ? 1 : (axis == 1 ? (long long)nz : (long long)ny * nz);
-            const CroftSched sc = croft_pass_sched(n, M == 1 ? LAYOUT_ROW : LAYOUT_COL, dtype == CROFT_C2C_F64 ? 16 : 8);
+            const CroftSched sc = croft_pass_sched_v(n, M == 1 ? LAYOUT_ROW : LAYOUT_COL, dtype == CROFT_C2C_F64 ? 16 : 8,
+                                                     p->axis_kind[axis] == 0 ? p->axis_sv[axis] : 0);
             ns = sc.count;
             for (int i = 0; i < ns; ++i) rad[i] = sc.r[i];
         }
@@ -469,8 +488,237 @@ croft_status croft_plan_create(croft_plan* out, int nx, int ny, int nz, croft_dt
     return create_impl(out, nx, ny, nz, dtype, CROFT_SCHEDULE_AUTO);
 }
 
+static croft_status exec_dir(croft_plan plan, const void* in, void* out, void* stream, float isign);
+
+}  // extern "C"
+
+// ---------------------------------------------------------------------------
+// CROFT_SCHEDULE_TUNED: measure the alternatives at plan creation, keep the fastest
+// ---------------------------------------------------------------------------
+// The paper tunes its implementation by hand through options 1-4 and the chunk count K
+// (Sec. 5.1); here the choices a plan can make are timed on the device at creation:
+//  * per axis, the pass kernel: for the column passes of 32-thread pencils (270..512 points)
+//    the 16- or 8-column tile, each with the near-equal or the radix-16-first power-of-two
+//    split, and the tensor-copy ring kernel; every other pass has one kernel;
+//  * the schedule (the transpose fusion): three passes with the chosen kernels, z+y per L2
+//    slab, or the fused yz-plane pass, as whole forward+backward transforms.
+// Each candidate axis kernel is timed inside a three-pass plan by that plan's per-pass events
+// (the other axes on the rules), five runs after two warm-ups, median.  The choice is cached
+// on disk (CROFT_TUNE_CACHE, as for batched plans) keyed by the shape, dtype, GPU name and
+// CUDA runtime version.
+
+static std::string plan_tune_key(int nx, int ny, int nz, croft_dtype dtype) {
+    int dev = 0, rt = 0;
+    cudaGetDevice(&dev);
+    cudaRuntimeGetVersion(&rt);
+    cudaDeviceProp prop;
+    cudaGetDeviceProperties(&prop, dev);
+    char buf[512];
+    snprintf(buf, sizeof(buf), "plan-v1:%dx%dx%d:%d:%s:%d", nx, ny, nz, (int)dtype, prop.name, rt);
+    for (char* c = buf; *c; ++c)
+        if (*c == ' ' || *c == '"') *c = '_';
+    return buf;
+}
+
+static std::string plan_tune_cache_path() {
+    const char* p = getenv("CROFT_TUNE_CACHE");
+    if (p && *p) return p;
+    const char* home = getenv("HOME");
+    return std::string(home && *home ? home : "/tmp") + "/.croft_tune_cache.txt";
+}
+
+static bool plan_tune_lookup(const std::string& key, int* sched, AxisChoice* ch) {
+    FILE* f = fopen(plan_tune_cache_path().c_str(), "r");
+    if (!f) return false;
+    char line[2048];
+    bool found = false;
+    while (fgets(line, sizeof(line), f)) {
+        char k[900];
+        int v[10];
+        if (sscanf(line, "%899s %d %d %d %d %d %d %d %d %d %d", k, &v[0], &v[1], &v[2], &v[3], &v[4], &v[5], &v[6], &v[7],
+                   &v[8], &v[9]) == 11 &&
+            key == k) {
+            *sched = v[0];
+            for (int a = 0; a < 3; ++a) {
+                ch->kind[a] = v[1 + 3 * a];
+                ch->w[a] = v[2 + 3 * a];
+                ch->sv[a] = v[3 + 3 * a];
+            }
+            found = true;  // the last matching line wins
+        }
+    }
+    fclose(f);
+    return found;
+}
+
+static void plan_tune_store(const std::string& key, int sched, const AxisChoice& ch, const std::string& info) {
+    FILE* f = fopen(plan_tune_cache_path().c_str(), "a");
+    if (!f) return;
+    fprintf(f, "%s %d %d %d %d %d %d %d %d %d %d %s\n", key.c_str(), sched, ch.kind[0], ch.w[0], ch.sv[0], ch.kind[1],
+            ch.w[1], ch.sv[1], ch.kind[2], ch.w[2], ch.sv[2], info.c_str());
+    fclose(f);
+}
+
+// Median of `reps` timings (ms) of fn() on stream s after `warm` untimed runs; < 0 on failure.
+template <class F>
+static double time_median(F fn, cudaStream_t s, int warm, int reps) {
+    cudaEvent_t a, b;
+    if (cudaEventCreate(&a) != cudaSuccess || cudaEventCreate(&b) != cudaSuccess) {
+        cudaGetLastError();
+        return -1;
+    }
+    std::vector<float> t;
+    bool ok = true;
+    for (int r = 0; r < warm + reps && ok; ++r) {
+        cudaEventRecord(a, s);
+        ok = fn();
+        cudaEventRecord(b, s);
+        if (cudaEventSynchronize(b) != cudaSuccess) ok = false;
+        float ms = 0.f;
+        cudaEventElapsedTime(&ms, a, b);
+        if (r >= warm) t.push_back(ms);
+    }
+    cudaEventDestroy(a);
+    cudaEventDestroy(b);
+    if (!ok) {
+        cudaGetLastError();
+        return -1;
+    }
+    std::sort(t.begin(), t.end());
+    return t[t.size() / 2];
+}
+
+// ms of the pass of `axis` in a three-pass plan with kernel choice ch (median of per-pass events).
+static double time_axis_pass(int nx, int ny, int nz, const AxisChoice& ch, int axis, void* x, void* y, cudaStream_t s) {
+    croft_plan p = nullptr;
+    if (create_impl(&p, nx, ny, nz, CROFT_C2C_F32, CROFT_SCHEDULE_THREE_PASS, &ch) != CROFT_OK) {
+        cudaGetLastError();
+        return -1;
+    }
+    int idx = -1;
+    for (size_t i = 0; i < p->passes.size(); ++i)
+        if (p->pass_axis[i] == axis) idx = (int)i;
+    std::vector<float> t;
+    if (idx >= 0 && croft_plan_set_timing(p, 1) == CROFT_OK) {
+        for (int r = 0; r < 7; ++r) {
+            if (exec_dir(p, x, y, s, 1.0f) != CROFT_OK) break;
+            float ms[8];
+            const int np = croft_plan_pass_times(p, ms, 8);
+            if (np <= idx) break;
+            if (r >= 2) t.push_back(ms[idx]);
+        }
+    }
+    croft_plan_destroy(p);
+    if (t.size() < 5) return -1;
+    std::sort(t.begin(), t.end());
+    return t[t.size() / 2];
+}
+
+static croft_status create_tuned(croft_plan* out, int nx, int ny, int nz, croft_dtype dtype) {
+    if (!out) return CROFT_ERR_INVALID_ARG;
+    // tensor-core and complex128 plans have one kernel per pass: nothing to choose
+    if (dtype != CROFT_C2C_F32) return create_impl(out, nx, ny, nz, dtype, CROFT_SCHEDULE_THREE_PASS);
+    if (!axis_supported(nx) || !axis_supported(ny) || !axis_supported(nz)) return CROFT_ERR_UNSUPPORTED_SIZE;
+    const std::string key = plan_tune_key(nx, ny, nz, dtype);
+    int sched = CROFT_SCHEDULE_THREE_PASS;
+    AxisChoice ch;
+    if (plan_tune_lookup(key, &sched, &ch)) {
+        croft_status st = create_impl(out, nx, ny, nz, dtype, (croft_schedule)sched, &ch);
+        if (st == CROFT_OK) (*out)->tuned = "tuned (cached)";
+        return st;
+    }
+    const long long N = (long long)nx * ny * nz;
+    const size_t bytes = (size_t)N * sizeof(float2);
+    void* x = nullptr;
+    void* y = nullptr;
+    if (dev_alloc(&x, bytes) != cudaSuccess || dev_alloc(&y, bytes) != cudaSuccess) {
+        cudaGetLastError();
+        dev_free(x);
+        dev_free(y);
+        return create_impl(out, nx, ny, nz, dtype, CROFT_SCHEDULE_AUTO);  // no room to measure: the rules
+    }
+    cudaStream_t s = nullptr;
+    cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking);
+    cudaMemsetAsync(x, 0, bytes, s);
+    std::string info;
+    char tmp[256];
+    static const char* an[3] = {"x", "y", "z"};
+    const int dims[3] = {nx, ny, nz};
+    for (int axis = 2; axis >= 0; --axis) {
+        const int n = dims[axis];
+        const long long M = (axis == 2) ? 1 : (axis == 1 ? (long long)nz : (long long)ny * nz);
+        if (n == 1 || M == 1 || croft_threads_per_pencil(n) != 32) continue;  // one kernel: nothing to choose
+        struct Cand {
+            int kind, w, sv;
+        };
+        std::vector<Cand> cands = {{-1, 0, 0}};
+        for (int sv = 0; sv < croft_sched_variants(n, LAYOUT_COL, 8); ++sv)
+            for (int w : {croft_col_width(n, 8), kColNarrowWidth}) cands.push_back({0, w, sv});
+        cands.push_back({1, 16, 0});
+        double best = 1e30;
+        Cand pick = cands[0];
+        for (const Cand& c : cands) {
+            AxisChoice trial = ch;
+            trial.kind[axis] = c.kind;
+            trial.w[axis] = c.w;
+            trial.sv[axis] = c.sv;
+            const double ms = time_axis_pass(nx, ny, nz, trial, axis, x, y, s);
+            snprintf(tmp, sizeof(tmp), "%s%s:%s", info.empty() ? "" : " ", an[axis],
+                     c.kind < 0 ? "rules" : (c.kind == 1 ? "ring" : (c.sv ? "r16" : "even")));
+            info += tmp;
+            if (c.kind == 0) {
+                snprintf(tmp, sizeof(tmp), "/w%d", c.w);
+                info += tmp;
+            }
+            snprintf(tmp, sizeof(tmp), "=%.1fus", ms < 0 ? -1.0 : ms * 1e3);
+            info += tmp;
+            if (ms > 0 && ms < best * 0.995) {  // a candidate must win by more than noise to replace an earlier one
+                best = ms;
+                pick = c;
+            }
+        }
+        ch.kind[axis] = pick.kind;
+        ch.w[axis] = pick.w;
+        ch.sv[axis] = pick.sv;
+    }
+    // the schedule, as whole forward+backward transforms
+    const croft_schedule scheds[3] = {CROFT_SCHEDULE_THREE_PASS, CROFT_SCHEDULE_SLAB_L2, CROFT_SCHEDULE_PLANE_FUSED};
+    static const char* sn[3] = {"three_pass", "slab_l2", "plane_fused"};
+    double best = 1e30;
+    for (int k = 0; k < 3; ++k) {
+        croft_plan p = nullptr;
+        const croft_status st = create_impl(&p, nx, ny, nz, dtype, scheds[k], k == 0 ? &ch : nullptr);
+        if (st != CROFT_OK) {
+            cudaGetLastError();
+            continue;
+        }
+        const double ms = time_median(
+            [&]() { return exec_dir(p, x, y, s, 1.0f) == CROFT_OK && exec_dir(p, y, y, s, -1.0f) == CROFT_OK; }, s, 2, 5);
+        croft_plan_destroy(p);
+        snprintf(tmp, sizeof(tmp), " %s=%.1fus", sn[k], ms * 1e3);
+        info += tmp;
+        if (ms > 0 && ms < best * 0.995) {
+            best = ms;
+            sched = scheds[k];
+        }
+    }
+    cudaStreamSynchronize(s);
+    cudaStreamDestroy(s);
+    dev_free(x);
+    dev_free(y);
+    cudaGetLastError();
+    if (sched != CROFT_SCHEDULE_THREE_PASS) ch = AxisChoice();  // the other schedules run the rules' kernels
+    plan_tune_store(key, sched, ch, info);
+    croft_status st = create_impl(out, nx, ny, nz, dtype, (croft_schedule)sched, &ch);
+    if (st == CROFT_OK) (*out)->tuned = "tuned: " + info;
+    return st;
+}
+
+extern "C" {
+
 croft_status croft_plan_create_schedule(croft_plan* out, int nx, int ny, int nz, croft_dtype dtype,
                                         croft_schedule schedule) {
+    if (schedule == CROFT_SCHEDULE_TUNED) return create_tuned(out, nx, ny, nz, dtype);
     return create_impl(out, nx, ny, nz, dtype, schedule);
 }
 
@@ -495,7 +743,7 @@ int croft_plan_describe(croft_plan plan, char* buf, int cap) {
         snprintf(tmp, sizeof(tmp), " | %s:%s%s%s n=%d radix=", an[plan->pass_axis[i]], L.layout == LAYOUT_ROW ? "row" : "col",
                  L.tc ? (L.tc == 2 ? "+tc_fp16x3" : "+tc_bf16x3") : "", L.ring ? "+ring" : "", L.args.n);
         s += tmp;
-        CroftSched sc = L.tc ? croft_make_sched_tc(L.args.n) : croft_pass_sched(L.args.n, L.layout, L.f64 ? 16 : 8);
+        CroftSched sc = L.tc ? croft_make_sched_tc(L.args.n) : croft_pass_sched_v(L.args.n, L.layout, L.f64 ? 16 : 8, L.sv);
         for (int st = 0; st < sc.count; ++st) {
             snprintf(tmp, sizeof(tmp), "%s%d", st ? "x" : "", sc.r[st]);
             s += tmp;
@@ -511,6 +759,7 @@ int croft_plan_describe(croft_plan plan, char* buf, int cap) {
     } else {
         s += " | convolve: forward, multiply, backward";
     }
+    if (!plan->tuned.empty()) s += " | " + plan->tuned;
     }
     if (buf && cap > 0) {
         size_t m = s.size() < (size_t)(cap - 1) ? s.size() : (size_t)(cap - 1);

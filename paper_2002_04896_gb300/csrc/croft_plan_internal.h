@@ -2,6 +2,7 @@
 #pragma once
 #include <cuda_runtime.h>
 
+#include <string>
 #include <vector>
 
 #include "../../include/croft.h"
@@ -37,5 +38,11 @@ struct croft_plan_s {
     int conv_axis;                    // its axis (the plan's last pass)
     bool conv_fused;                  // false: croft_exec_convolve runs F, a multiply and B instead
     bool pdl;                         // launches after the first of an exec use programmatic dependent launch
+    // per-axis kernel choice (CROFT_SCHEDULE_TUNED): kind -1 the library's rules, 0 the plain pass
+    // kernel with tile width axis_w and schedule variant axis_sv, 1 the tensor-copy ring kernel
+    int axis_kind[3];
+    int axis_w[3];
+    int axis_sv[3];
+    std::string tuned;                // the tuner's choice and measurements (describe)
 };
 

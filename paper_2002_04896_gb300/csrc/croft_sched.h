@@ -154,6 +154,14 @@ CROFT_HD constexpr bool croft_even_pow2_pass(int n, int layout, int es) {
 CROFT_HD constexpr CroftSched croft_pass_sched(int n, int layout, int es) {
     return croft_make_sched(n, croft_even_pow2_pass(n, layout, es));
 }
+// Schedule variants a tuned plan may pick per pass (CROFT_SCHEDULE_TUNED): sv = 0 the rule
+// above; sv = 1 the other power-of-two split for the passes that have one built (the column
+// passes of complex64 32-thread pencils: the radix-16-first split instead of the near-equal
+// one).  croft_sched_variants(n, layout, es) is 2 for those passes, else 1.
+CROFT_HD constexpr int croft_sched_variants(int n, int layout, int es) { return croft_even_pow2_pass(n, layout, es) ? 2 : 1; }
+CROFT_HD constexpr CroftSched croft_pass_sched_v(int n, int layout, int es, int sv) {
+    return croft_make_sched(n, croft_even_pow2_pass(n, layout, es) && sv == 0);
+}
 
 // Column-tile width (columns per CTA) of a COL pass - a compile-time constant of
 // its kernel - for length n and complex element size es bytes: 16 columns
