@@ -27,6 +27,7 @@ struct PassArgs {
     const double2* tw64;        // complex128 passes: the twiddle table in double precision
     const unsigned char* tc_b;  // tensor-core passes: 16-point DFT matrix, bf16 hi | lo, core-matrix layout (4 KB)
     int* status;                // tensor-core passes: device status word (bounded waits), may be null
+    const float2* tw2;          // pair passes: the combine twiddles w_n^k, k < n/2
 };
 
 // Fused z+y pass: 2D FFT of every yz-plane (one plane per cluster of C CTAs).
@@ -44,6 +45,7 @@ typedef void (*conv_fn)(const float2*, float2*, const float*, const PassArgs);
 typedef void (*conv64_fn)(const double2*, double2*, const double*, const PassArgs);
 
 constexpr int kRingTileWidth = 16;  // columns per tile of the ring column kernel (128-byte rows)
+constexpr int kPairTileWidth = 16;  // columns per tile of the cluster-pair column kernel
 
 // Column pass fed by tensor copies through a ring of tile buffers (croft_ring_kernel.cuh).
 struct RingArgs {
@@ -79,6 +81,8 @@ struct PassLaunch {
     int tc;             // tensor-core variant of the pass kernel: 0 none, 1 + operand precision (TcPrec)
     int f64;            // 1: complex128 pass kernel
     int sv;             // schedule variant of a plain pass kernel (croft_pass_sched_v)
+    int th;             // threads per pencil of a plain COL pass kernel if not the rule's (0: the rule's)
+    int pair;           // 1: cluster-pair column kernel (croft_pair_kernel.cuh)
     int ring;           // 1: tensor-copy ring kernel (RingArgs below)
     RingArgs ra;
     long long B;        // ring: outer extent of the tensor map (batch rows)
@@ -94,13 +98,18 @@ const PlaneKernel* find_plane_kernel(int ny, int nz, int cluster);
 
 // croft_ring.cu: the tensor-copy ring column kernel (NULL if not instantiated for n)
 ring_fn ring_kernel_for(int n);
+// croft_pair.cu: the cluster-pair column kernel (NULL if not instantiated for n)
+pass_fn pair_kernel_for(int n);
+// Launch shape of a pair column pass (2-CTA clusters over 16-column tiles); false when the
+// pass does not qualify or no cluster fits.
+bool shape_pair(PassLaunch& L, int n, long long M, long long ncols);
 
 // croft_kernels.cu, one per size group (w: the COL tile width, ignored for ROW; sv: the
-// schedule variant, croft_pass_sched_v)
-pass_fn lookup_pass_kernel_group_0(int layout, int n, int w, int sv);
-pass_fn lookup_pass_kernel_group_1(int layout, int n, int w, int sv);
-pass_fn lookup_pass_kernel_group_2(int layout, int n, int w, int sv);
-pass_fn lookup_pass_kernel_group_3(int layout, int n, int w, int sv);
+// schedule variant, croft_pass_sched_v; th: threads per pencil if not the rule's, else 0)
+pass_fn lookup_pass_kernel_group_0(int layout, int n, int w, int sv, int th);
+pass_fn lookup_pass_kernel_group_1(int layout, int n, int w, int sv, int th);
+pass_fn lookup_pass_kernel_group_2(int layout, int n, int w, int sv, int th);
+pass_fn lookup_pass_kernel_group_3(int layout, int n, int w, int sv, int th);
 
 // croft_tc.cu: tensor-core pass kernels (NULL when n has no instantiation); prec 0 = split
 // bf16, 1 = split fp16 with per-butterfly power-of-two scaling (TcPrec)
@@ -131,8 +140,8 @@ cudaError_t launch_scale(const void* in, void* out, const void* g, long long n, 
 extern int g_max_smem;  // the device's opt-in shared memory per block (set by plan creation)
 // Launch shape of one axis pass (tile width, block, grid, shared memory); false when no shape fits.
 bool shape_pass(PassLaunch& L, int layout, int n, long long M, long long ncols, int tc = 0, bool f64 = false,
-                int want_w = 0, int sv = 0);
-pass_fn pass_kernel_for(int layout, int n, int w, int sv = 0);
+                int want_w = 0, int sv = 0, int th = 0);
+pass_fn pass_kernel_for(int layout, int n, int w, int sv = 0, int th = 0);
 conv_fn conv_kernel_for(int n);
 // Launch shape of a ring column pass (one persistent CTA per SM); false when the pass does not
 // qualify (length, odd stride, shared memory).

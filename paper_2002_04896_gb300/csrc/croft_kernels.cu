@@ -17,9 +17,14 @@ namespace croft {
 // for tuned plans, both widths with the other schedule variant (sv = 1).
 // w: the width asked for (nullptr when no kernel is built for it).
 template <int N>
-static pass_fn col_kernel(int w, int sv) {
+static pass_fn col_kernel(int w, int sv, int th) {
     constexpr int W = croft_col_width(N, 8);
     if constexpr (croft_threads_per_pencil(N) == 32 && W != kColNarrowWidth) {
+        // 16 threads per pencil (32 elements each): 256-thread CTAs of 16 columns, three per SM
+        if (th == 16 && w == W)
+            return sv ? croft_pass_kernel_bounded<LAYOUT_COL, N, float2, W, 3, W * 16, 1, 16>
+                      : croft_pass_kernel_bounded<LAYOUT_COL, N, float2, W, 3, W * 16, 0, 16>;
+        if (th) return nullptr;
         if (w == kColNarrowWidth)
             return sv ? croft_pass_kernel_bounded<LAYOUT_COL, N, float2, kColNarrowWidth, croft_col_narrow_minb(N),
                                                   kColNarrowWidth * 32, 1>
@@ -27,7 +32,7 @@ static pass_fn col_kernel(int w, int sv) {
                                                   kColNarrowWidth * 32>;
         if (w == W && sv) return croft_pass_kernel_bounded<LAYOUT_COL, N, float2, W, croft_col_minb(N, 8), 512, 1>;
     }
-    if (w != W || sv) return nullptr;
+    if (w != W || sv || th) return nullptr;
     if constexpr (croft_col_minb(N, 8) > 1) return croft_pass_kernel_bounded<LAYOUT_COL, N, float2, W, croft_col_minb(N, 8)>;
     else if constexpr (croft_pass_minb(N, 8) > 0)
         return croft_pass_kernel_bounded<LAYOUT_COL, N, float2, W, croft_pass_minb(N, 8), 256>;
@@ -40,9 +45,9 @@ static pass_fn row_kernel() {
     else return croft_pass_kernel<LAYOUT_ROW, N>;
 }
 
-pass_fn CROFT_CAT(lookup_pass_kernel_group_, CROFT_GROUP)(int layout, int n, int w, int sv) {
+pass_fn CROFT_CAT(lookup_pass_kernel_group_, CROFT_GROUP)(int layout, int n, int w, int sv, int th) {
 #define CROFT_CASE(N) \
-    case N: return layout == LAYOUT_ROW ? (sv ? nullptr : row_kernel<N>()) : col_kernel<N>(w, sv);
+    case N: return layout == LAYOUT_ROW ? ((sv || th) ? nullptr : row_kernel<N>()) : col_kernel<N>(w, sv, th);
     switch (n) {
         CROFT_CAT(CROFT_SIZES_, CROFT_GROUP)(CROFT_CASE)
         default: return nullptr;

@@ -29,9 +29,9 @@ namespace croft {
 // (complex64, the default) or double2 (complex128, twiddles from A.tw64).
 // COL kernels are specialised on the column-tile width WC as well (so the
 // shared-memory indices fold into constants); ROW kernels take W from A.W.
-template <int LAYOUT, int N, class C, int WC, int SV = 0>
+template <int LAYOUT, int N, class C, int WC, int SV = 0, int TH = 0>
 __device__ __forceinline__ void pass_body(const C* in, C* out, const PassArgs& A) {
-    constexpr int T = croft_threads_per_pencil(N);
+    constexpr int T = TH > 0 ? TH : croft_threads_per_pencil(N);  // TH: threads per pencil, if not the rule's
     extern __shared__ __align__(16) unsigned char smem_raw[];
     C* smem = reinterpret_cast<C*>(smem_raw);
     C* stw = smem;
@@ -82,10 +82,10 @@ __global__ void __launch_bounds__(512) croft_pass_kernel(const C* in, C* out, co
 
 // The same with registers bounded for MINB CTAs of MAXT threads per SM (croft_col_minb,
 // croft_pass_minb); SV selects the schedule variant (croft_pass_sched_v).
-template <int LAYOUT, int N, class C, int WC, int MINB, int MAXT = 512, int SV = 0>
+template <int LAYOUT, int N, class C, int WC, int MINB, int MAXT = 512, int SV = 0, int TH = 0>
 __global__ void __launch_bounds__(MAXT, MINB) croft_pass_kernel_bounded(const C* in, C* out,
                                                                          const __grid_constant__ PassArgs A) {
-    pass_body<LAYOUT, N, C, WC, SV>(in, out, A);
+    pass_body<LAYOUT, N, C, WC, SV, TH>(in, out, A);
 }
 
 }  // namespace croft

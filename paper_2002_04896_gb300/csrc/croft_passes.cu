@@ -17,18 +17,20 @@ int g_max_smem = 0;
 // COL: W adjacent columns per CTA, W a multiple of 16 (128-byte rows).
 // Aim for ~256 threads per CTA and <= 100 KB of shared memory so that at
 // least two CTAs share an SM.
-bool shape_pass(PassLaunch& L, int layout, int n, long long M, long long ncols, int tc, bool f64, int want_w, int sv) {
+bool shape_pass(PassLaunch& L, int layout, int n, long long M, long long ncols, int tc, bool f64, int want_w, int sv,
+                int th) {
     memset(&L, 0, sizeof(L));
     L.layout = layout;
     L.tc = tc;
     L.sv = sv;
+    L.th = (layout == LAYOUT_COL && !tc && !f64) ? th : 0;
     L.f64 = f64 ? 1 : 0;
     const long long es = f64 ? 16 : 8;  // bytes per element
     PassArgs& A = L.args;
     A.n = n;
     A.M = M;
     A.ncols = ncols;
-    const int T = croft_threads_per_pencil(n);
+    const int T = L.th > 0 ? L.th : croft_threads_per_pencil(n);
     L.T = T;
     A.tw_pad = ((n + 1) / 2) * 2;  // keeps the tile 16-byte aligned
     const long long smem_cap = 100 * 1024;
@@ -99,6 +101,60 @@ static bool encode_ring_map(const PassLaunch& L, const float2* src, CUtensorMap*
                CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
 }
 
+static cudaLaunchConfig_t pair_config(const PassLaunch& L, cudaStream_t s, cudaLaunchAttribute* attr, bool pdl) {
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3((unsigned)L.grid, 1, 1);
+    cfg.blockDim = dim3((unsigned)L.block, 1, 1);
+    cfg.dynamicSmemBytes = (size_t)L.smem;
+    cfg.stream = s;
+    attr[0].id = cudaLaunchAttributeClusterDimension;
+    attr[0].val.clusterDim.x = 2;
+    attr[0].val.clusterDim.y = 1;
+    attr[0].val.clusterDim.z = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    if (pdl) {
+        attr[1].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+        attr[1].val.programmaticStreamSerializationAllowed = 1;
+        cfg.numAttrs = 2;
+    }
+    return cfg;
+}
+
+bool shape_pair(PassLaunch& L, int n, long long M, long long ncols) {
+    memset(&L, 0, sizeof(L));
+    pass_fn f = pair_kernel_for(n);
+    if (!f || n % 2 || M < 1 || ncols % M != 0) return false;
+    const int n2 = n / 2;
+    L.kind = PASS_AXIS;
+    L.layout = LAYOUT_COL;
+    L.pair = 1;
+    L.T = croft_threads_per_pencil(n2);
+    PassArgs& A = L.args;
+    A.n = n;
+    A.M = M;
+    A.ncols = ncols;
+    A.W = kPairTileWidth;
+    A.tw_pad = ((n2 + 1) / 2) * 2;
+    L.block = kPairTileWidth * L.T;
+    L.smem = (A.tw_pad + (n2 + (n2 & 1)) + n2 * kPairTileWidth) * (int)sizeof(float2);
+    const long long grid = 2 * ((ncols + kPairTileWidth - 1) / kPairTileWidth);
+    if (grid > 0x7fffffffLL || L.smem > g_max_smem) return false;
+    L.grid = (int)grid;
+    if (L.smem > 48 * 1024 && cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, L.smem) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    cudaLaunchAttribute attr[2];
+    cudaLaunchConfig_t cfg = pair_config(L, 0, attr, false);
+    int clusters = 0;
+    if (cudaOccupancyMaxActiveClusters(&clusters, f, &cfg) != cudaSuccess || clusters < 1) {
+        cudaGetLastError();
+        return false;
+    }
+    return true;
+}
+
 bool shape_ring(PassLaunch& L, int n, long long M, long long ncols) {
     memset(&L, 0, sizeof(L));
     ring_fn f = ring_kernel_for(n);
@@ -142,11 +198,11 @@ bool shape_ring(PassLaunch& L, int n, long long M, long long ncols) {
     return L.grid > 0 && tensor_map_encoder() != nullptr;
 }
 
-pass_fn pass_kernel_for(int layout, int n, int w, int sv) {
-    pass_fn f = lookup_pass_kernel_group_0(layout, n, w, sv);
-    if (!f) f = lookup_pass_kernel_group_1(layout, n, w, sv);
-    if (!f) f = lookup_pass_kernel_group_2(layout, n, w, sv);
-    if (!f) f = lookup_pass_kernel_group_3(layout, n, w, sv);
+pass_fn pass_kernel_for(int layout, int n, int w, int sv, int th) {
+    pass_fn f = lookup_pass_kernel_group_0(layout, n, w, sv, th);
+    if (!f) f = lookup_pass_kernel_group_1(layout, n, w, sv, th);
+    if (!f) f = lookup_pass_kernel_group_2(layout, n, w, sv, th);
+    if (!f) f = lookup_pass_kernel_group_3(layout, n, w, sv, th);
     return f;
 }
 
@@ -216,6 +272,7 @@ cudaError_t prepare_pass(const PassLaunch& L) {
         if (e != cudaSuccess) return e;
         return nclusters > 0 ? cudaSuccess : cudaErrorInvalidConfiguration;
     }
+    if (L.pair) return pair_kernel_for(L.args.n) ? cudaSuccess : cudaErrorInvalidValue;
     if (L.ring) {
         ring_fn f = ring_kernel_for(L.args.n);
         if (!f || !tensor_map_encoder()) return cudaErrorInvalidValue;
@@ -228,7 +285,7 @@ cudaError_t prepare_pass(const PassLaunch& L) {
         if (L.smem <= 48 * 1024) return cudaSuccess;
         return cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, L.smem);
     }
-    pass_fn f = L.tc ? tc_pass_kernel_for(L.layout, L.args.n, L.tc - 1) : pass_kernel_for(L.layout, L.args.n, L.args.W, L.sv);
+    pass_fn f = L.tc ? tc_pass_kernel_for(L.layout, L.args.n, L.tc - 1) : pass_kernel_for(L.layout, L.args.n, L.args.W, L.sv, L.th);
     if (!f) return cudaErrorInvalidValue;
     if (L.smem <= 48 * 1024) return cudaSuccess;
     return cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, L.smem);
@@ -248,6 +305,13 @@ cudaError_t launch_pass(const PassLaunch& L, const void* vin, void* vout, cudaSt
         cudaLaunchConfig_t cfg = plane_config(L, s, attr, pdl);
         return cudaLaunchKernelEx(&cfg, L.pk.fn, in, out, L.pargs);
     }
+    if (L.pair) {
+        pass_fn f = pair_kernel_for(L.args.n);
+        if (!f) return cudaErrorInvalidValue;
+        cudaLaunchAttribute attr[2];
+        cudaLaunchConfig_t cfg = pair_config(L, s, attr, pdl);
+        return cudaLaunchKernelEx(&cfg, f, in, out, L.args);
+    }
     if (L.ring) {
         ring_fn f = ring_kernel_for(L.args.n);
         if (!f) return cudaErrorInvalidValue;
@@ -266,7 +330,7 @@ cudaError_t launch_pass(const PassLaunch& L, const void* vin, void* vout, cudaSt
         f<<<L.grid, L.block, L.smem, s>>>(in, out, L.args);
         return cudaGetLastError();
     }
-    pass_fn f = pass_kernel_for(L.layout, L.args.n, L.args.W, L.sv);
+    pass_fn f = pass_kernel_for(L.layout, L.args.n, L.args.W, L.sv, L.th);
     if (!f) return cudaErrorInvalidValue;
     return launch_ex(f, L, s, pdl, in, out, L.args);
 }

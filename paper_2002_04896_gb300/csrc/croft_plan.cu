@@ -146,8 +146,10 @@ croft_status croft_plan_destroy(croft_plan plan) {
     int cur = -1;
     cudaGetDevice(&cur);
     cudaSetDevice(plan->device);
-    for (int a = 0; a < 3; ++a)
+    for (int a = 0; a < 3; ++a) {
         dev_free(plan->tw_dev[a]);
+        dev_free(plan->tw_pair[a]);
+    }
     for (cudaEvent_t e : plan->ev)
         if (e) cudaEventDestroy(e);
     if (plan->batch) batch_state_destroy(plan->batch);
@@ -185,6 +187,44 @@ static croft_status add_axis_pass(croft_plan p, int axis, int x0 = 0, int nxs = 
     const char* re = getenv("CROFT_RING");
     const bool ring_pass = layout == LAYOUT_COL && !f64 && !p->axis_tc[axis] &&
                            (kind >= 0 ? kind == 1 : (re ? re[0] == '1' : croft_ring_default(n, 8, M * 8)));
+    // The cluster-pair kernel (croft_pair_kernel.cuh): tuned plans (kind 2) or CROFT_PAIR=1.
+    const char* pe = getenv("CROFT_PAIR");
+    const bool pair_pass = layout == LAYOUT_COL && !f64 && !p->axis_tc[axis] && !ring_pass &&
+                           (kind >= 0 ? kind == 2 : (pe ? pe[0] == '1' : croft_pair_default(n, 8, M * 8)));
+    if (pair_pass) {
+        PassLaunch L;
+        if (shape_pair(L, n, M, N / n)) {
+            const int n2 = n / 2;
+            if (!p->tw_pair[axis]) {
+                // [the half length's table in its column schedule | w_n^k, k < n/2], float64 -> float32
+                std::vector<float> tw(4 * (size_t)n2 + 2, 0.f);
+                const CroftSched hs = croft_pass_sched(n2, LAYOUT_COL, 8);
+                if (n2 > 1 && build_twiddles(n2, hs.r, hs.count, tw.data()) != n2 - 1) return CROFT_ERR_UNSUPPORTED_SIZE;
+                for (int k = 0; k < n2; ++k) {
+                    double re, im;
+                    twiddle64(k, n, &re, &im);
+                    tw[2 * ((size_t)n2 + k)] = (float)re;
+                    tw[2 * ((size_t)n2 + k) + 1] = (float)im;
+                }
+                if (dev_alloc((void**)&p->tw_pair[axis], sizeof(float2) * 2 * (size_t)n2) != cudaSuccess) return CROFT_ERR_OOM;
+                if (cudaMemcpy(p->tw_pair[axis], tw.data(), sizeof(float2) * 2 * (size_t)n2, cudaMemcpyHostToDevice) != cudaSuccess)
+                    return CROFT_ERR_CUDA;
+            }
+            L.args.tw = p->tw_pair[axis];
+            L.args.tw2 = p->tw_pair[axis] + n2;
+            L.args.status = p->d_status;
+            L.offset = offset;
+            L.src_in = sin;
+            L.group = grp;
+            if (prepare_pass(L) == cudaSuccess) {
+                p->passes.push_back(L);
+                p->pass_axis.push_back(axis);
+                if (grp >= p->ngroups) p->ngroups = grp + 1;
+                return CROFT_OK;
+            }
+            cudaGetLastError();
+        }
+    }
     if (ring_pass) {
         PassLaunch L;
         if (shape_ring(L, n, M, N / n)) {
@@ -203,8 +243,17 @@ static croft_status add_axis_pass(croft_plan p, int axis, int x0 = 0, int nxs = 
         }
     }
     PassLaunch L;
-    const int want_w = kind == 0 ? p->axis_w[axis] : 0, sv = kind == 0 ? p->axis_sv[axis] : 0;
-    if (!shape_pass(L, layout, n, M, N / n, p->axis_tc[axis] ? 1 + p->tc_prec : 0, f64, want_w, sv))
+    int want_w = kind == 0 ? p->axis_w[axis] : 0, sv = kind == 0 ? p->axis_sv[axis] : 0;
+    int th = kind == 0 ? p->axis_th[axis] : 0;
+    // CROFT_COL_TH=16 (measurement): 16-column tiles with 16 threads per pencil for every column
+    // pass of 32-thread pencils that a plan's rules would give the plain kernel
+    const char* te = getenv("CROFT_COL_TH");
+    if (kind < 0 && te && atoi(te) == 16 && layout == LAYOUT_COL && !f64 && !p->axis_tc[axis] &&
+        croft_threads_per_pencil(n) == 32) {
+        th = 16;
+        want_w = croft_col_width(n, 8);
+    }
+    if (!shape_pass(L, layout, n, M, N / n, p->axis_tc[axis] ? 1 + p->tc_prec : 0, f64, want_w, sv, th))
         return CROFT_ERR_UNSUPPORTED_SIZE;
     L.kind = PASS_AXIS;
     L.args.tw = p->tw_dev[axis];
@@ -322,6 +371,7 @@ struct AxisChoice {
     int kind[3] = {-1, -1, -1};
     int w[3] = {0, 0, 0};
     int sv[3] = {0, 0, 0};
+    int th[3] = {0, 0, 0};
 };
 
 static croft_status create_impl(croft_plan* out, int nx, int ny, int nz, croft_dtype dtype, croft_schedule sched,
@@ -356,7 +406,10 @@ static croft_status create_impl(croft_plan* out, int nx, int ny, int nz, croft_d
     p->dims[2] = nz;
     p->dtype = dtype;
     p->device = dev;
-    for (int a = 0; a < 3; ++a) p->tw_dev[a] = NULL;
+    for (int a = 0; a < 3; ++a) {
+        p->tw_dev[a] = NULL;
+        p->tw_pair[a] = NULL;
+    }
     p->timing = false;
     p->ev_count = 0;
     p->ngroups = 0;
@@ -371,6 +424,7 @@ static croft_status create_impl(croft_plan* out, int nx, int ny, int nz, croft_d
         p->axis_kind[a] = choice ? choice->kind[a] : -1;
         p->axis_w[a] = choice ? choice->w[a] : 0;
         p->axis_sv[a] = choice ? choice->sv[a] : 0;
+        p->axis_th[a] = choice ? choice->th[a] : 0;
     }
     const char* pdl_env = getenv("CROFT_PDL");  // 0: ordinary stream ordering between passes (for measurement)
     p->pdl = !(pdl_env && pdl_env[0] == '0');
@@ -514,7 +568,7 @@ static std::string plan_tune_key(int nx, int ny, int nz, croft_dtype dtype) {
     cudaDeviceProp prop;
     cudaGetDeviceProperties(&prop, dev);
     char buf[512];
-    snprintf(buf, sizeof(buf), "plan-v1:%dx%dx%d:%d:%s:%d", nx, ny, nz, (int)dtype, prop.name, rt);
+    snprintf(buf, sizeof(buf), "plan-v2:%dx%dx%d:%d:%s:%d", nx, ny, nz, (int)dtype, prop.name, rt);
     for (char* c = buf; *c; ++c)
         if (*c == ' ' || *c == '"') *c = '_';
     return buf;
@@ -534,15 +588,16 @@ static bool plan_tune_lookup(const std::string& key, int* sched, AxisChoice* ch)
     bool found = false;
     while (fgets(line, sizeof(line), f)) {
         char k[900];
-        int v[10];
-        if (sscanf(line, "%899s %d %d %d %d %d %d %d %d %d %d", k, &v[0], &v[1], &v[2], &v[3], &v[4], &v[5], &v[6], &v[7],
-                   &v[8], &v[9]) == 11 &&
+        int v[13];
+        if (sscanf(line, "%899s %d %d %d %d %d %d %d %d %d %d %d %d %d", k, &v[0], &v[1], &v[2], &v[3], &v[4], &v[5],
+                   &v[6], &v[7], &v[8], &v[9], &v[10], &v[11], &v[12]) == 14 &&
             key == k) {
             *sched = v[0];
             for (int a = 0; a < 3; ++a) {
-                ch->kind[a] = v[1 + 3 * a];
-                ch->w[a] = v[2 + 3 * a];
-                ch->sv[a] = v[3 + 3 * a];
+                ch->kind[a] = v[1 + 4 * a];
+                ch->w[a] = v[2 + 4 * a];
+                ch->sv[a] = v[3 + 4 * a];
+                ch->th[a] = v[4 + 4 * a];
             }
             found = true;  // the last matching line wins
         }
@@ -554,8 +609,9 @@ static bool plan_tune_lookup(const std::string& key, int* sched, AxisChoice* ch)
 static void plan_tune_store(const std::string& key, int sched, const AxisChoice& ch, const std::string& info) {
     FILE* f = fopen(plan_tune_cache_path().c_str(), "a");
     if (!f) return;
-    fprintf(f, "%s %d %d %d %d %d %d %d %d %d %d %s\n", key.c_str(), sched, ch.kind[0], ch.w[0], ch.sv[0], ch.kind[1],
-            ch.w[1], ch.sv[1], ch.kind[2], ch.w[2], ch.sv[2], info.c_str());
+    fprintf(f, "%s %d", key.c_str(), sched);
+    for (int a = 0; a < 3; ++a) fprintf(f, " %d %d %d %d", ch.kind[a], ch.w[a], ch.sv[a], ch.th[a]);
+    fprintf(f, " %s\n", info.c_str());
     fclose(f);
 }
 
@@ -649,12 +705,15 @@ static croft_status create_tuned(croft_plan* out, int nx, int ny, int nz, croft_
         const long long M = (axis == 2) ? 1 : (axis == 1 ? (long long)nz : (long long)ny * nz);
         if (n == 1 || M == 1 || croft_threads_per_pencil(n) != 32) continue;  // one kernel: nothing to choose
         struct Cand {
-            int kind, w, sv;
+            int kind, w, sv, th;
         };
-        std::vector<Cand> cands = {{-1, 0, 0}};
-        for (int sv = 0; sv < croft_sched_variants(n, LAYOUT_COL, 8); ++sv)
-            for (int w : {croft_col_width(n, 8), kColNarrowWidth}) cands.push_back({0, w, sv});
-        cands.push_back({1, 16, 0});
+        std::vector<Cand> cands = {{-1, 0, 0, 0}};
+        for (int sv = 0; sv < croft_sched_variants(n, LAYOUT_COL, 8); ++sv) {
+            for (int w : {croft_col_width(n, 8), kColNarrowWidth}) cands.push_back({0, w, sv, 0});
+            cands.push_back({0, croft_col_width(n, 8), sv, 16});  // 16 threads per pencil
+        }
+        cands.push_back({1, 16, 0, 0});
+        if (n % 2 == 0) cands.push_back({2, 16, 0, 0});  // the cluster pair
         double best = 1e30;
         Cand pick = cands[0];
         for (const Cand& c : cands) {
@@ -662,12 +721,13 @@ static croft_status create_tuned(croft_plan* out, int nx, int ny, int nz, croft_
             trial.kind[axis] = c.kind;
             trial.w[axis] = c.w;
             trial.sv[axis] = c.sv;
+            trial.th[axis] = c.th;
             const double ms = time_axis_pass(nx, ny, nz, trial, axis, x, y, s);
             snprintf(tmp, sizeof(tmp), "%s%s:%s", info.empty() ? "" : " ", an[axis],
-                     c.kind < 0 ? "rules" : (c.kind == 1 ? "ring" : (c.sv ? "r16" : "even")));
+                     c.kind < 0 ? "rules" : (c.kind == 1 ? "ring" : (c.kind == 2 ? "pair" : (c.sv ? "r16" : "even"))));
             info += tmp;
             if (c.kind == 0) {
-                snprintf(tmp, sizeof(tmp), "/w%d", c.w);
+                snprintf(tmp, sizeof(tmp), "/w%d%s", c.w, c.th ? "/t16" : "");
                 info += tmp;
             }
             snprintf(tmp, sizeof(tmp), "=%.1fus", ms < 0 ? -1.0 : ms * 1e3);
@@ -680,6 +740,7 @@ static croft_status create_tuned(croft_plan* out, int nx, int ny, int nz, croft_
         ch.kind[axis] = pick.kind;
         ch.w[axis] = pick.w;
         ch.sv[axis] = pick.sv;
+        ch.th[axis] = pick.th;
     }
     // the schedule, as whole forward+backward transforms
     const croft_schedule scheds[3] = {CROFT_SCHEDULE_THREE_PASS, CROFT_SCHEDULE_SLAB_L2, CROFT_SCHEDULE_PLANE_FUSED};
@@ -741,9 +802,14 @@ int croft_plan_describe(croft_plan plan, char* buf, int cap) {
             continue;
         }
         snprintf(tmp, sizeof(tmp), " | %s:%s%s%s n=%d radix=", an[plan->pass_axis[i]], L.layout == LAYOUT_ROW ? "row" : "col",
-                 L.tc ? (L.tc == 2 ? "+tc_fp16x3" : "+tc_bf16x3") : "", L.ring ? "+ring" : "", L.args.n);
+                 L.tc ? (L.tc == 2 ? "+tc_fp16x3" : "+tc_bf16x3") : "", L.ring ? "+ring" : (L.pair ? "+pair" : ""),
+                 L.args.n);
         s += tmp;
         CroftSched sc = L.tc ? croft_make_sched_tc(L.args.n) : croft_pass_sched_v(L.args.n, L.layout, L.f64 ? 16 : 8, L.sv);
+        if (L.pair) {  // radix 2 across the pair over the half length's schedule
+            sc = croft_pass_sched(L.args.n / 2, LAYOUT_COL, 8);
+            s += "2|";
+        }
         for (int st = 0; st < sc.count; ++st) {
             snprintf(tmp, sizeof(tmp), "%s%d", st ? "x" : "", sc.r[st]);
             s += tmp;

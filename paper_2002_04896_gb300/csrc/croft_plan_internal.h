@@ -23,6 +23,7 @@ struct croft_plan_s {
     std::vector<croft::PassLaunch> passes;   // execution order (z, y, x; length-1 axes skipped)
     std::vector<int> pass_axis;       // axis index of each pass (2 = z, 1 = y, 0 = x)
     float2* tw_dev[3];                // per-axis twiddle tables (NULL for length <= 1)
+    float2* tw_pair[3];               // pair column passes: [half-length table | combine twiddles], else NULL
     bool timing;
     std::vector<cudaEvent_t> ev;      // one per logical pass + 1 (created when timing is enabled)
     int ev_count;                     // events recorded by the last exec
@@ -39,10 +40,12 @@ struct croft_plan_s {
     bool conv_fused;                  // false: croft_exec_convolve runs F, a multiply and B instead
     bool pdl;                         // launches after the first of an exec use programmatic dependent launch
     // per-axis kernel choice (CROFT_SCHEDULE_TUNED): kind -1 the library's rules, 0 the plain pass
-    // kernel with tile width axis_w and schedule variant axis_sv, 1 the tensor-copy ring kernel
+    // kernel with tile width axis_w and schedule variant axis_sv, 1 the tensor-copy ring kernel,
+    // 2 the cluster-pair kernel
     int axis_kind[3];
     int axis_w[3];
     int axis_sv[3];
+    int axis_th[3];                   // threads per pencil of a tuned plain column kernel (0: the rule's)
     std::string tuned;                // the tuner's choice and measurements (describe)
 };
 

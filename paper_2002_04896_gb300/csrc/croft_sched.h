@@ -224,3 +224,14 @@ CROFT_HD constexpr int croft_conv_width(int n, int es) { return croft_col_width(
 CROFT_HD constexpr bool croft_ring_default(int n, int es, long long stride_bytes) {
     return false && es == 8 && croft_threads_per_pencil(n) == 32 && stride_bytes > 16 * 1024;
 }
+
+// Whether a column pass runs the cluster-pair kernel (croft_pair_kernel.cuh) by default: the
+// 512-point axes whose elements lie at least 256 KB apart (the x pass of grids well beyond the
+// L2), where each half of the pair is a 256-point column transform (16 x 16, the best-tuned
+// half).  Per-pass CUDA events, plain vs pair, ms: 512^3 x 0.488 / 0.425, 512x512x256 x 0.245 /
+// 0.217, 512x256x256 x 0.125 / 0.112; it loses below that stride (512x128x128 x 0.029 / 0.032),
+// on the 4 KB-stride y pass (512^3 y 0.400 / 0.407) and for the other even lengths (480^3 x
+// 0.348 / 0.363, 384x360x320 x 0.127 / 0.168), where the tuner can still pick it.
+CROFT_HD constexpr bool croft_pair_default(int n, int es, long long stride_bytes) {
+    return es == 8 && n == 512 && stride_bytes >= 256 * 1024;
+}

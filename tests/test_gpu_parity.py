@@ -86,11 +86,16 @@ def test_long_pencil_x_pass_over_wide_stride(croft_lib, dev, n):
 
 
 def test_column_width_follows_the_stride(croft_lib, dev):
-    """512^3: the y pass (4 KB stride) runs 8-column tiles, the x pass (2 MB stride) 16."""
+    """512^3: the y pass (4 KB stride) runs 8-column tiles, the x pass (2 MB stride) 16-column
+    tiles split over a cluster pair of 256-thread CTAs; below 256 KB strides the plain
+    16-column, 512-thread tile."""
     with croft_lib.Plan(512, 512, 512) as p:
         d = p.describe()
     assert " W=8 block=256 " in _pass_desc(d, "y"), d
-    assert " W=16 block=512 " in _pass_desc(d, "x"), d
+    assert "+pair" in _pass_desc(d, "x") and " W=16 block=256 " in _pass_desc(d, "x"), d
+    with croft_lib.Plan(512, 128, 128) as p:
+        d = p.describe()
+    assert "+pair" not in d and " W=16 block=512 " in _pass_desc(d, "x"), d
 
 
 @pytest.mark.parametrize("shape", [(1, 1, 1), (1, 1, 8), (1, 16, 1), (32, 1, 1), (2, 2, 2), (6, 10, 15),

@@ -2,8 +2,8 @@
 correctly, and a measured plan matches the oracle.
 
 The tuner times, per column pass of a 270..512-point axis, the 16- and 8-column tiles with the
-near-equal and the radix-16-first power-of-two split and the tensor-copy ring kernel, then the
-schedules, and caches the choice.  The candidates are driven one by one through the cache
+near-equal and the radix-16-first power-of-two split, 16-column tiles with 16 threads per pencil,
+and the tensor-copy ring kernel, then the schedules, and caches the choice.  The candidates are driven one by one through the cache
 file (its last matching line wins): the first plan writes the key, the test appends a line per
 forced configuration.
 """
@@ -65,19 +65,22 @@ def test_every_tuner_candidate_matches_the_oracle(croft_lib, cache, n):
         x = _noise(shape, n + axis)
         desc = _check(croft_lib, x, ("tuned: ",))  # measured: writes the cache line
         lines = open(cache).read().splitlines()
-        key = [ln for ln in lines if ln.startswith(f"plan-v1:{shape[0]}x{shape[1]}x{shape[2]}:0:")][-1].split()[0]
+        key = [ln for ln in lines if ln.startswith(f"plan-v2:{shape[0]}x{shape[1]}x{shape[2]}:0:")][-1].split()[0]
         assert "three_pass=" in desc and "slab_l2=" in desc
-        for kind, w, sv in ((0, 16, 0), (0, 8, 0), (0, 16, 1), (0, 8, 1), (1, 16, 0)):
-            ch = [[-1, 0, 0] for _ in range(3)]
-            ch[axis] = [kind, w, sv]
+        for kind, w, sv, th in ((0, 16, 0, 0), (0, 8, 0, 0), (0, 16, 1, 0), (0, 8, 1, 0), (0, 16, 0, 16),
+                                (0, 16, 1, 16), (1, 16, 0, 0)) + (((2, 16, 0, 0),) if n % 2 == 0 else ()):
+            ch = [[-1, 0, 0, 0] for _ in range(3)]
+            ch[axis] = [kind, w, sv, th]
             with open(cache, "a") as f:
                 f.write(f"{key} 1 " + " ".join(str(v) for c in ch for v in c) + " forced\n")
             desc = _check(croft_lib, x, ("tuned (cached)",))
             seg = [s for s in desc.split("|") if s.strip().startswith(("x:", "y:", "z:"))][2 - axis]
             if kind == 1:
                 assert "+ring" in seg, seg
+            elif kind == 2:
+                assert "+pair" in seg, seg
             else:
-                assert f" W={w} " in seg, seg
+                assert f" W={w} " in seg and f" T={th or 32} " in seg, seg
                 if n == 512:
                     assert ("radix=16x16x2" in seg) == (sv == 1), seg
 
