@@ -127,15 +127,31 @@ __device__ __forceinline__ void tc_ld32(uint32_t taddr, float* out) {
 struct TcCtx {
     unsigned char* abuf;  // A hi (G*8 KB) then A lo (G*8 KB), aliases the pass tile
     uint32_t b_hi;        // shared address of B hi (2 KB) and B lo (+2 KB)
-    uint32_t mbar;
+    uint32_t mbar;        // the (first) mbarrier; per-group scope: group g's at mbar + 8 g
     uint32_t tmem;        // TMEM base (lane 0, first column); group g uses columns 32g..32g+31
     int groups;           // blockDim / 128
     int* status;          // device status word (timeout), may be null
+    int gstride;          // per-group scope: bytes between the groups' operand buffers in the tile
+};
+
+// Synchronisation scope of a tensor-core pass.  GS = false: the CTA (__syncthreads; one thread
+// issues every group's MMAs).  GS = true: each 128-thread GEMM group on its own (named barrier
+// 1 + g, its own mbarrier, issuer and A operands): row passes whose groups own whole pencils,
+// so that one group's MMA round trip overlaps another group's operand preparation.
+template <bool GS>
+__device__ __forceinline__ void tc_sync(int g) {
+    if constexpr (GS) asm volatile("bar.sync %0, 128;" ::"r"(1 + g) : "memory");
+    else __syncthreads();
+}
+template <bool GS>
+struct TcBarrier {
+    int g;
+    __device__ __forceinline__ void operator()() const { tc_sync<GS>(g); }
 };
 
 // Radix-16 stage S of the (Tc16Sched) schedule on the tensor cores; at most one butterfly per
 // thread (threads past the N/16 butterflies of a pencil contribute zero GEMM rows).
-template <class SchedT, int S, int T, int PREC, class Src, class Dst>
+template <class SchedT, int S, int T, int PREC, bool GS, class Src, class Dst>
 __device__ __forceinline__ void fft_stage_tc16(const Src& src, const Dst& dst, const float2* stw, int lane, bool ok_pencil,
                                                const TcCtx& tc, uint32_t parity) {
     constexpr int N = SchedT::N;
@@ -160,7 +176,9 @@ __device__ __forceinline__ void fft_stage_tc16(const Src& src, const Dst& dst, c
 #pragma unroll
         for (int j = 0; j < 16; ++j) u[j] = make_float2(0.f, 0.f);
     }
-    __syncthreads();  // every input of the stage read before the tile becomes the operand buffer
+    const int tid = threadIdx.x;
+    const int g = tid >> 7, r = tid & 127;
+    tc_sync<GS>(g);  // every input of the stage read before the tile becomes the operand buffer
 
     // fp16 operands: scale the butterfly by 2^sh so that its largest component lies in
     // [2^14, 2^15) (exact; undone on the outputs below)
@@ -175,10 +193,9 @@ __device__ __forceinline__ void fft_stage_tc16(const Src& src, const Dst& dst, c
         unscale = __uint_as_float((uint32_t)(127 - sh) << 23);
     }
     // A row for this butterfly: k < 16 real parts, k >= 16 imaginary parts; hi and lo halves
-    const int tid = threadIdx.x;
-    const int g = tid >> 7, r = tid & 127;
-    unsigned char* ahi = tc.abuf + g * 8192;
-    unsigned char* alo = tc.abuf + tc.groups * 8192 + g * 8192;
+    // (per-group operands lie in the group's own part of the tile: tc.gstride bytes apart)
+    unsigned char* ahi = GS ? tc.abuf + g * tc.gstride : tc.abuf + g * 8192;
+    unsigned char* alo = GS ? ahi + 8192 : tc.abuf + tc.groups * 8192 + g * 8192;
 #pragma unroll
     for (int kk = 0; kk < 4; ++kk) {
         uint32_t h[4], l[4];
@@ -194,14 +211,15 @@ __device__ __forceinline__ void fft_stage_tc16(const Src& src, const Dst& dst, c
     }
     asm volatile("fence.proxy.async.shared::cta;");  // generic-proxy smem writes -> tensor core
     asm volatile("tcgen05.fence::before_thread_sync;");
-    __syncthreads();
+    tc_sync<GS>(g);
     asm volatile("tcgen05.fence::after_thread_sync;");
-    if (tid == 0) {
+    const uint32_t mbar = GS ? tc.mbar + 8 * g : tc.mbar;  // (per-group mbarriers 8 bytes apart)
+    if (GS ? r == 0 : tid == 0) {
         const uint32_t a_hi = smem_addr(tc.abuf);
-        const uint32_t a_lo = a_hi + tc.groups * 8192;
-        for (int gg = 0; gg < tc.groups; ++gg) {
+        for (int gg = GS ? g : 0; gg < (GS ? g + 1 : tc.groups); ++gg) {
             const uint32_t d = tc.tmem + 32 * gg;
-            const uint32_t ah = a_hi + gg * 8192, al = a_lo + gg * 8192;
+            const uint32_t ah = GS ? a_hi + gg * tc.gstride : a_hi + gg * 8192;
+            const uint32_t al = GS ? ah + 8192 : a_hi + tc.groups * 8192 + gg * 8192;
             uint32_t acc = 0;
 #pragma unroll
             for (int ks = 0; ks < 2; ++ks) {  // K = 32 as two K = 16 steps
@@ -211,12 +229,13 @@ __device__ __forceinline__ void fft_stage_tc16(const Src& src, const Dst& dst, c
                 tc_mma<PREC>(d, tc_desc(al + ks * 256), tc_desc(tc.b_hi + ks * 256), 1);
             }
         }
-        asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(tc.mbar));
+        asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(mbar));
     }
-    // one warp waits for the MMAs' commit (bounded), the others at the CTA barrier (no polling);
-    // the barrier then orders every thread's TMEM reads after the completed MMAs
-    if (tid < 32 && !tc_wait(tc.mbar, parity) && tc.status && tid == 0) atomicExch(tc.status, 5 /* CROFT_ERR_TIMEOUT */);
-    __syncthreads();
+    // one warp (of the group / of the CTA) waits for the MMAs' commit (bounded), the others at
+    // the barrier (no polling); the barrier then orders every thread's TMEM reads after the MMAs
+    if ((GS ? r : tid) < 32 && !tc_wait(mbar, parity) && tc.status && (GS ? r : tid) == 0)
+        atomicExch(tc.status, 5 /* CROFT_ERR_TIMEOUT */);
+    tc_sync<GS>(g);
     asm volatile("tcgen05.fence::after_thread_sync;");
     float d[32];
     const int warp = tid >> 5;
@@ -260,20 +279,20 @@ struct TcStageInfo {
 };
 
 // One stage with the given operands: radix-16 stages on the tensor cores, others on CUDA cores.
-template <class SchedT, int S, int T, int PREC, class Src, class Dst>
+template <class SchedT, int S, int T, int PREC, bool GS, class Src, class Dst>
 __device__ __forceinline__ void tc_run_stage(const Src& src, const Dst& dst, const float2* stw, int lane, bool ok,
                                              const TcCtx& tc, int tc_index) {
     using I = TcStageInfo<SchedT, S>;
     if constexpr (I::tc) {
-        fft_stage_tc16<SchedT, S, T, PREC>(src, dst, stw, lane, ok, tc, (uint32_t)(tc_index & 1));
+        fft_stage_tc16<SchedT, S, T, PREC, GS>(src, dst, stw, lane, ok, tc, (uint32_t)(tc_index & 1));
     } else if constexpr (I::first) {
         fft_stage_s<SchedT, S, T>(src, NoBarrier{}, dst, stw, lane, ok);
     } else {
-        fft_stage_s<SchedT, S, T>(src, CtaBarrier{}, dst, stw, lane, ok);
+        fft_stage_s<SchedT, S, T>(src, TcBarrier<GS>{(int)threadIdx.x >> 7}, dst, stw, lane, ok);
     }
 }
 
-template <class SchedT, int S, int LAYOUT, int T, int PREC>
+template <class SchedT, int S, int LAYOUT, int T, int PREC, bool GS>
 __device__ __forceinline__ void tc_stages(const float2* gin, float2* gout, float2* tile, const float2* stw,
                                           const PassArgs& A, int c, int lane, bool ok, long long M, const TcCtx& tc,
                                           int tc_index) {
@@ -282,27 +301,28 @@ __device__ __forceinline__ void tc_stages(const float2* gin, float2* gout, float
     if constexpr (LAYOUT == LAYOUT_ROW) {
         const SmemRow sm{tile + c * row_ld(N)};
         if constexpr (I::first && I::last)
-            tc_run_stage<SchedT, S, T, PREC>(GlobalInUnit{gin, A.isign}, GlobalOutUnit{gout, A.isign}, stw, lane, ok, tc, tc_index);
+            tc_run_stage<SchedT, S, T, PREC, GS>(GlobalInUnit{gin, A.isign}, GlobalOutUnit{gout, A.isign}, stw, lane, ok, tc, tc_index);
         else if constexpr (I::first)
-            tc_run_stage<SchedT, S, T, PREC>(GlobalInUnit{gin, A.isign}, sm, stw, lane, ok, tc, tc_index);
+            tc_run_stage<SchedT, S, T, PREC, GS>(GlobalInUnit{gin, A.isign}, sm, stw, lane, ok, tc, tc_index);
         else if constexpr (I::last)
-            tc_run_stage<SchedT, S, T, PREC>(sm, GlobalOutUnit{gout, A.isign}, stw, lane, ok, tc, tc_index);
+            tc_run_stage<SchedT, S, T, PREC, GS>(sm, GlobalOutUnit{gout, A.isign}, stw, lane, ok, tc, tc_index);
         else
-            tc_run_stage<SchedT, S, T, PREC>(sm, sm, stw, lane, ok, tc, tc_index);
+            tc_run_stage<SchedT, S, T, PREC, GS>(sm, sm, stw, lane, ok, tc, tc_index);
     } else {
         const SmemCol sm{tile + c, A.W};
         if constexpr (I::first && I::last)
-            tc_run_stage<SchedT, S, T, PREC>(GlobalIn{gin, M, A.isign}, GlobalOut{gout, M, A.isign}, stw, lane, ok, tc, tc_index);
+            tc_run_stage<SchedT, S, T, PREC, GS>(GlobalIn{gin, M, A.isign}, GlobalOut{gout, M, A.isign}, stw, lane, ok, tc, tc_index);
         else if constexpr (I::first)
-            tc_run_stage<SchedT, S, T, PREC>(GlobalIn{gin, M, A.isign}, sm, stw, lane, ok, tc, tc_index);
+            tc_run_stage<SchedT, S, T, PREC, GS>(GlobalIn{gin, M, A.isign}, sm, stw, lane, ok, tc, tc_index);
         else if constexpr (I::last)
-            tc_run_stage<SchedT, S, T, PREC>(sm, GlobalOut{gout, M, A.isign}, stw, lane, ok, tc, tc_index);
+            tc_run_stage<SchedT, S, T, PREC, GS>(sm, GlobalOut{gout, M, A.isign}, stw, lane, ok, tc, tc_index);
         else
-            tc_run_stage<SchedT, S, T, PREC>(sm, sm, stw, lane, ok, tc, tc_index);
+            tc_run_stage<SchedT, S, T, PREC, GS>(sm, sm, stw, lane, ok, tc, tc_index);
     }
     if constexpr (!I::last) {
-        __syncthreads();
-        tc_stages<SchedT, S + 1, LAYOUT, T, PREC>(gin, gout, tile, stw, A, c, lane, ok, M, tc, tc_index + (I::tc ? 1 : 0));
+        tc_sync<GS>((int)threadIdx.x >> 7);
+        tc_stages<SchedT, S + 1, LAYOUT, T, PREC, GS>(gin, gout, tile, stw, A, c, lane, ok, M, tc,
+                                                      tc_index + (I::tc ? 1 : 0));
     }
 }
 
@@ -313,8 +333,12 @@ __global__ void __launch_bounds__(512) croft_pass_kernel_tc(const float2* in, fl
                                                              const __grid_constant__ PassArgs A) {
     using SchedT = Tc16Sched<N>;
     constexpr int T = croft_threads_per_pencil(N);
+    // per-group scope for row passes whose 128-thread groups own whole pencils and whose pencils
+    // of one group hold that group's 16 KB of operands (16-byte aligned)
+    constexpr int kGroupBytes = (128 / T) * croft_row_ld(N) * (int)sizeof(float2);
+    constexpr bool GS = LAYOUT == LAYOUT_ROW && T <= 128 && 128 % T == 0 && kGroupBytes >= 16384 && kGroupBytes % 16 == 0;
     extern __shared__ __align__(16) float2 smem[];
-    __shared__ __align__(8) uint64_t mbar;
+    __shared__ __align__(8) uint64_t mbar[4];
     __shared__ uint32_t tmem_slot;
     float2* stw = smem;
     unsigned char* bmat = (unsigned char*)(smem + A.tw_pad);
@@ -326,7 +350,7 @@ __global__ void __launch_bounds__(512) croft_pass_kernel_tc(const float2* in, fl
     int ncols = 32;
     while (ncols < 32 * groups) ncols <<= 1;
     if (tid == 0) {
-        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_addr(&mbar)));
+        for (int k = 0; k < 4; ++k) asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_addr(&mbar[k])));
         asm volatile("fence.mbarrier_init.release.cluster;");
     }
     if (tid < 32) {
@@ -338,7 +362,7 @@ __global__ void __launch_bounds__(512) croft_pass_kernel_tc(const float2* in, fl
     asm volatile("tcgen05.fence::before_thread_sync;");
     __syncthreads();
     asm volatile("tcgen05.fence::after_thread_sync;");
-    const TcCtx tc{(unsigned char*)tile, smem_addr(bmat), smem_addr(&mbar), tmem_slot, groups, A.status};
+    const TcCtx tc{(unsigned char*)tile, smem_addr(bmat), smem_addr(&mbar[0]), tmem_slot, groups, A.status, kGroupBytes};
 
     int lane, c;
     long long base, M = 1;
@@ -360,7 +384,7 @@ __global__ void __launch_bounds__(512) croft_pass_kernel_tc(const float2* in, fl
         const long long m = cc - b * M;
         base = b * (long long)N * M + m;
     }
-    tc_stages<SchedT, 0, LAYOUT, T, PREC>(in + base, out + base, tile, stw, A, c, lane, ok, M, tc, 0);
+    tc_stages<SchedT, 0, LAYOUT, T, PREC, GS>(in + base, out + base, tile, stw, A, c, lane, ok, M, tc, 0);
 
     asm volatile("tcgen05.fence::before_thread_sync;");
     __syncthreads();
