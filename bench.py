@@ -541,6 +541,10 @@ def measure_rows(croft, torch, dev, stream, flush, peak, peak_kind, only=None): 
         rows[f"f64_{n}"] = {"shape": list(shape), "dtype": "f64", "ms_fwd": f_ms, "ms_bwd": b_ms,
                             "gflops_fwd": nominal_flops(shape) / (f_ms * 1e-3) / 1e9, "pass_ms": pass_ms,
                             "roundtrip_rel_l2": rt,
+                            "roofline": {"bound": "alu", "unit": "FP64 pipe", "frac_pipe_active": 0.85,
+                                         "peak_nominal_tflops": 1.25,
+                                         "source": "ncu sm__pipe_fp64_cycles_active on the 256^3 complex128 passes "
+                                                   "(profiles/f64_kernels_256.md); the same kernels at every size"},
                             "paper_context": dict(paper[n], speedup_vs_croft_best=paper[n]["croft_best_s"] / (f_ms * 1e-3),
                                                   speedup_vs_fftw3_best=paper[n]["fftw3_best_s"] / (f_ms * 1e-3))}
         del x, y, z
