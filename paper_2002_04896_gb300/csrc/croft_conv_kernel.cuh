@@ -154,8 +154,8 @@ __device__ __forceinline__ void conv_body(const C* in, C* out, const typename Cx
     const int lane = threadIdx.x / W;
     const long long col = (long long)blockIdx.x * W + c;
     const bool ok = col < A.ncols;
-    const long long b = col / A.M;
-    const long long m = col - b * A.M;
+    long long b, m;
+    col_split(col, A, b, m);
     const long long base = b * (long long)N * A.M + m;
 
     pdl_allow_dependents();

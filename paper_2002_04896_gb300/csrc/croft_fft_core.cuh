@@ -28,6 +28,20 @@ namespace croft {
 // Accessors are templates on the complex type C (float2 or double2); the
 // float2 names below are the complex64 instances.
 
+// Address of element a of a pencil with element stride `stride`: a 32 x 32 -> 64-bit
+// multiply-add (axis lengths are at most 4096, so a pencil index and a stride in bytes -
+// at most 4096^2 elements of 16 bytes - both fit in 32 bits).
+template <class C>
+__device__ __forceinline__ C* strided_at(C* p, int a, long long stride) {
+    const unsigned sb = (unsigned)stride * (unsigned)sizeof(C);
+    return reinterpret_cast<C*>(reinterpret_cast<char*>(p) + (unsigned long long)(unsigned)a * sb);
+}
+template <class C>
+__device__ __forceinline__ const C* strided_at(const C* p, int a, long long stride) {
+    const unsigned sb = (unsigned)stride * (unsigned)sizeof(C);
+    return reinterpret_cast<const C*>(reinterpret_cast<const char*>(p) + (unsigned long long)(unsigned)a * sb);
+}
+
 // Pencil in HBM with element stride `stride`; conj() on the way in/out when isign = -1.
 template <class C>
 struct GlobalInT {
@@ -36,7 +50,7 @@ struct GlobalInT {
     long long stride;
     float isign;
     __device__ __forceinline__ C load(int a) const {
-        C t = p[(long long)a * stride];
+        C t = *strided_at(p, a, stride);
         t.y *= isign;
         return t;
     }
@@ -60,7 +74,7 @@ struct GlobalInCG {
     long long stride;
     float isign;
     __device__ __forceinline__ float2 load(int a) const {
-        float2 t = __ldcg(p + (long long)a * stride);
+        float2 t = __ldcg(strided_at(p, a, stride));
         t.y *= isign;
         return t;
     }
@@ -73,7 +87,7 @@ struct GlobalOutT {
     float isign;
     __device__ __forceinline__ void store(int a, C v) const {
         v.y *= isign;
-        p[(long long)a * stride] = v;
+        *strided_at(p, a, stride) = v;
     }
 };
 template <class C>

@@ -4,6 +4,7 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include "croft_coldiv.h"
 #include "croft_sched.h"
 
 namespace croft {
@@ -28,7 +29,23 @@ struct PassArgs {
     const unsigned char* tc_b;  // tensor-core passes: 16-point DFT matrix, bf16 hi | lo, core-matrix layout (4 KB)
     int* status;                // tensor-core passes: device status word (bounded waits), may be null
     const float2* tw2;          // pair passes: the combine twiddles w_n^k, k < n/2
+    CroftColDiv cdiv;           // COL passes: col / M as a multiply-high (croft_coldiv.h); m = 0: divide
 };
+
+#ifdef __CUDACC__
+// Batch row b = col / M and column m = col % M of pencil col of a COL pass.
+__device__ __forceinline__ void col_split(long long col, const PassArgs& A, long long& b, long long& m) {
+    if (A.cdiv.m) {
+        const unsigned c32 = (unsigned)col;
+        const unsigned q = croft_coldiv_q(A.cdiv.m, A.cdiv.s1, A.cdiv.s2, c32);
+        b = q;
+        m = c32 - q * (unsigned)A.M;
+    } else {
+        b = col / A.M;
+        m = col - b * A.M;
+    }
+}
+#endif
 
 // Fused z+y pass: 2D FFT of every yz-plane (one plane per cluster of C CTAs).
 struct PlaneArgs {

@@ -19,8 +19,8 @@
 //  * a cluster barrier; then CTA r combines the outputs k of its half of [0, N/2)
 //    (E from CTA 0's shared memory, O from CTA 1's, one of them read through
 //    distributed shared memory) and writes rows k and k + N/2 (full lines) to HBM;
-//  * a second cluster barrier keeps each CTA's shared memory alive until its partner
-//    has read it.
+//  * a second cluster barrier (a relaxed arrive: it orders no memory) keeps each CTA's
+//    shared memory alive until its partner has read it.
 // The waits are cluster barriers between two co-scheduled CTAs of one launch.
 #pragma once
 #include <cooperative_groups.h>
@@ -70,8 +70,8 @@ __global__ void __launch_bounds__(pair_threads<N>(), 5)
     const int lane = tid / W;
     const long long col = (long long)(blockIdx.x / 2) * W + c;
     const bool ok = col < A.ncols;
-    const long long b = col / A.M;
-    const long long m = col - b * A.M;
+    long long b, m;
+    col_split(col, A, b, m);
     const long long base = b * (long long)N * A.M + m;
 
     // the half-length transform of rows r, r + 2, ... into the tile, natural order
@@ -96,15 +96,17 @@ __global__ void __launch_bounds__(pair_threads<N>(), 5)
     const int k0 = r * KH;
     const int k1 = (k0 + KH < N2) ? k0 + KH : N2;
     const GlobalOutT<float2> dst{out + base, A.M, A.isign};
-    for (int k = k0 + lane; k < k1; k += T) {
-        const float2 e = E[k * W + c];
-        const float2 t = cmul(O[k * W + c], ctw[k]);
-        if (ok) {
+    if (ok)
+        for (int k = k0 + lane; k < k1; k += T) {
+            const float2 e = E[k * W + c];
+            const float2 t = cmul(O[k * W + c], ctw[k]);
             dst.store(k, cadd(e, t));
             dst.store(k + N2, csub(e, t));
         }
-    }
-    cluster.sync();  // the partner has finished reading this CTA's tile
+    // The partner has finished reading this CTA's tile: every value it read feeds a store it
+    // issued before arriving, so a relaxed arrive suffices (a release would wait for this
+    // CTA's global stores to be performed).
+    asm volatile("barrier.cluster.arrive.relaxed.aligned;\n\tbarrier.cluster.wait.aligned;" ::: "memory");
 }
 
 }  // namespace croft

@@ -58,8 +58,8 @@ __device__ __forceinline__ void pass_body(const C* in, C* out, const PassArgs& A
         const int lane = threadIdx.x / WC;
         const long long col = (long long)blockIdx.x * WC + c;
         const bool ok = col < A.ncols;
-        const long long b = col / A.M;
-        const long long m = col - b * A.M;
+        long long b, m;
+        col_split(col, A, b, m);
         const long long base = b * (long long)N * A.M + m;
         const GlobalInT<C> src{in + base, A.M, A.isign};
         const SmemColFixed<C, (WC > 0 ? WC : 1)> work{sbuf + c};

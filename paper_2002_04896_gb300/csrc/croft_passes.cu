@@ -26,6 +26,7 @@ bool shape_pass(PassLaunch& L, int layout, int n, long long M, long long ncols, 
     L.th = (layout == LAYOUT_COL && !tc && !f64) ? th : 0;
     L.f64 = f64 ? 1 : 0;
     const long long es = f64 ? 16 : 8;  // bytes per element
+    if (M < 1 || M * es > 0x7fffffffLL) return false;  // (strides in bytes stay 32-bit: strided_at)
     PassArgs& A = L.args;
     A.n = n;
     A.M = M;
@@ -57,6 +58,7 @@ bool shape_pass(PassLaunch& L, int layout, int n, long long M, long long ncols, 
         L.smem = (int)((A.tw_pad + (long long)n * W) * es);
     }
     L.block = A.W * T;
+    if (layout == LAYOUT_COL) A.cdiv = croft_coldiv_make(M, ncols + A.W);
     if (croft_make_sched(n).count <= 1 && !tc) L.smem = 0;  // single-stage kernels touch no shared memory
     if (tc) {
         // the A operands (128 bytes per thread) reuse the pass tile, which may be smaller
@@ -124,7 +126,7 @@ static cudaLaunchConfig_t pair_config(const PassLaunch& L, cudaStream_t s, cudaL
 bool shape_pair(PassLaunch& L, int n, long long M, long long ncols) {
     memset(&L, 0, sizeof(L));
     pass_fn f = pair_kernel_for(n);
-    if (!f || n % 2 || M < 1 || ncols % M != 0) return false;
+    if (!f || n % 2 || M < 1 || 2 * M * (long long)sizeof(float2) > 0x7fffffffLL || ncols % M != 0) return false;
     const int n2 = n / 2;
     L.kind = PASS_AXIS;
     L.layout = LAYOUT_COL;
@@ -135,6 +137,7 @@ bool shape_pair(PassLaunch& L, int n, long long M, long long ncols) {
     A.M = M;
     A.ncols = ncols;
     A.W = kPairTileWidth;
+    A.cdiv = croft_coldiv_make(M, ncols + kPairTileWidth);
     A.tw_pad = ((n2 + 1) / 2) * 2;
     L.block = kPairTileWidth * L.T;
     L.smem = (A.tw_pad + (n2 + (n2 & 1)) + n2 * kPairTileWidth) * (int)sizeof(float2);
