@@ -124,6 +124,7 @@ croft_status group_state_build(const std::vector<int>& dims, const std::vector<i
                 const int nz = dims[3 * g + 2], ny = dims[3 * g + 1];
                 S.M = kAxis[p] == 2 ? 1 : (kAxis[p] == 1 ? (long long)nz : (long long)ny * nz);
                 S.ncols = N / n;
+                S.cdiv = croft_coldiv_make(S.M, S.ncols + L.W);
                 S.first_tile = (int)(cta.size() - L.cta_begin);
                 const long long tiles = (S.ncols + L.W - 1) / L.W;
                 const int seg_local = (int)segs.size() - L.seg_begin;

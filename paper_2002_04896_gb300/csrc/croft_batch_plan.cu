@@ -149,6 +149,7 @@ croft_status build_batch_tables(const std::vector<int>& dims, const std::vector<
             const int T = croft_threads_per_pencil(n);
             D.W[p] = (D.M[p] == 1) ? CROFT_BATCH_THREADS / T : batch_col_width(n);
             D.ntiles[p] = (int)((D.ncols[p] + D.W[p] - 1) / D.W[p]);
+            D.cdiv[p] = croft_coldiv_make(D.M[p], D.ncols[p] + D.W[p]);
             D.dep[p] = prev;
             if (D.first_pass < 0) D.first_pass = p;
             prev = p;

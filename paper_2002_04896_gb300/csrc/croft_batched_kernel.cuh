@@ -40,6 +40,7 @@ struct BatchGrid {
     int dep[3];         // pass this pass waits for (-1: none)
     int first_pass;     // first pass that runs (reads `in`; later passes read `out`)
     int tw_off[3];      // offset of the axis' twiddle table in the pool
+    CroftColDiv cdiv[3];  // col / M[pass] as a multiply-high (croft_coldiv.h; m = 0: divide)
 };
 
 struct BatchItem {
@@ -93,8 +94,16 @@ __device__ __noinline__ void batch_tile(const BatchGrid& G, int pass, int tile, 
         const long long col = (long long)tile * W + c;
         const bool ok = lane < T && col < G.ncols[pass];
         const long long cc = ok ? col : 0;
-        const long long b = cc / M;
-        const long long m = cc - b * M;
+        const CroftColDiv dv = G.cdiv[pass];
+        long long b, m;
+        if (dv.m) {
+            const unsigned q = croft_coldiv_q(dv.m, dv.s1, dv.s2, (unsigned)cc);
+            b = q;
+            m = (unsigned)cc - q * (unsigned)M;
+        } else {
+            b = cc / M;
+            m = cc - b * M;
+        }
         const long long base = b * (long long)N * M + m;
         fft_pencil<N, T>(GlobalInCG{in + base, M, isign}, SmemCol{sbuf + c, W},
                          GlobalOut{out + base, M, isign}, stw, lane, ok);

@@ -30,16 +30,18 @@ namespace croft {
 
 // Address of element a of a pencil with element stride `stride`: a 32 x 32 -> 64-bit
 // multiply-add (axis lengths are at most 4096, so a pencil index and a stride in bytes -
-// at most 4096^2 elements of 16 bytes - both fit in 32 bits).
+// at most 4096^2 elements of 16 bytes; the planners refuse strides of 2^31 bytes or more -
+// both fit in a signed 32-bit int; signed, so that a = lane + constant folds into one
+// multiply-add on a per-thread base).
 template <class C>
 __device__ __forceinline__ C* strided_at(C* p, int a, long long stride) {
-    const unsigned sb = (unsigned)stride * (unsigned)sizeof(C);
-    return reinterpret_cast<C*>(reinterpret_cast<char*>(p) + (unsigned long long)(unsigned)a * sb);
+    const int sb = (int)stride * (int)sizeof(C);
+    return reinterpret_cast<C*>(reinterpret_cast<char*>(p) + (long long)a * sb);
 }
 template <class C>
 __device__ __forceinline__ const C* strided_at(const C* p, int a, long long stride) {
-    const unsigned sb = (unsigned)stride * (unsigned)sizeof(C);
-    return reinterpret_cast<const C*>(reinterpret_cast<const char*>(p) + (unsigned long long)(unsigned)a * sb);
+    const int sb = (int)stride * (int)sizeof(C);
+    return reinterpret_cast<const C*>(reinterpret_cast<const char*>(p) + (long long)a * sb);
 }
 
 // Pencil in HBM with element stride `stride`; conj() on the way in/out when isign = -1.

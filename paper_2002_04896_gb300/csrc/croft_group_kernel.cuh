@@ -20,7 +20,7 @@ struct GroupSeg {
     long long M;        // element stride of the axis (1 for a ROW pass)
     long long ncols;    // pencils of this grid along the axis
     int first_tile;     // first CTA of this grid in the launch
-    int pad_;
+    CroftColDiv cdiv;   // COL: col / M as a multiply-high (croft_coldiv.h; m = 0: divide)
 };
 
 struct GroupArgs {
@@ -62,8 +62,15 @@ __global__ void __launch_bounds__(256) croft_group_kernel(const __grid_constant_
         const int lane = threadIdx.x / WC;
         const long long col = tile * WC + c;
         const bool ok = col < S.ncols;
-        const long long b = col / S.M;
-        const long long m = col - b * S.M;
+        long long b, m;
+        if (S.cdiv.m) {
+            const unsigned q = croft_coldiv_q(S.cdiv.m, S.cdiv.s1, S.cdiv.s2, (unsigned)col);
+            b = q;
+            m = (unsigned)col - q * (unsigned)S.M;
+        } else {
+            b = col / S.M;
+            m = col - b * S.M;
+        }
         const long long base = b * (long long)N * S.M + m;
         fft_pencil<N, T>(GlobalIn{S.in + base, S.M, A.isign}, SmemColFixed<float2, WC>{sbuf + c},
                          GlobalOut{S.out + base, S.M, A.isign}, stw, lane, ok);

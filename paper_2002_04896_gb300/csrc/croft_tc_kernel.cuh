@@ -379,9 +379,8 @@ __global__ void __launch_bounds__(512) croft_pass_kernel_tc(const float2* in, fl
         const long long col = (long long)blockIdx.x * A.W + c;
         ok = col < A.ncols;
         M = A.M;
-        const long long cc = ok ? col : 0;
-        const long long b = cc / M;
-        const long long m = cc - b * M;
+        long long b, m;
+        col_split(ok ? col : 0, A, b, m);
         base = b * (long long)N * M + m;
     }
     tc_stages<SchedT, 0, LAYOUT, T, PREC, GS>(in + base, out + base, tile, stw, A, c, lane, ok, M, tc, 0);
