@@ -73,8 +73,8 @@ def measured_peaks():
 PASS_KERNEL_SOURCES = ("croft_butterflies.cuh", "croft_fft_core.cuh", "croft_internal.h", "croft_kernels.cu",
                        "croft_pass_kernel.cuh", "croft_passes.cu", "croft_row_layouts.h",
                        "croft_sched.h", "croft_sizes.h", "croft_ring_kernel.cuh", "croft_ring.cu",
-                       "croft_pair_kernel.cuh", "croft_pair.cu")
-TC_KERNEL_SOURCES = PASS_KERNEL_SOURCES + ("croft_tc_kernel.cuh", "croft_tc.cu")
+                       "croft_pair_kernel.cuh", "croft_pair.cu", "croft_coldiv.h")
+TC_KERNEL_SOURCES = PASS_KERNEL_SOURCES + ("croft_tc_kernel.cuh", "croft_tc.cu", "croft_tc_operand.h")
 
 
 def kernel_source_sha(names=PASS_KERNEL_SOURCES) -> str:

@@ -28,22 +28,6 @@ namespace croft {
 // Accessors are templates on the complex type C (float2 or double2); the
 // float2 names below are the complex64 instances.
 
-// Address of element a of a pencil with element stride `stride`: a 32 x 32 -> 64-bit
-// multiply-add (axis lengths are at most 4096, so a pencil index and a stride in bytes -
-// at most 4096^2 elements of 16 bytes; the planners refuse strides of 2^31 bytes or more -
-// both fit in a signed 32-bit int; signed, so that a = lane + constant folds into one
-// multiply-add on a per-thread base).
-template <class C>
-__device__ __forceinline__ C* strided_at(C* p, int a, long long stride) {
-    const int sb = (int)stride * (int)sizeof(C);
-    return reinterpret_cast<C*>(reinterpret_cast<char*>(p) + (long long)a * sb);
-}
-template <class C>
-__device__ __forceinline__ const C* strided_at(const C* p, int a, long long stride) {
-    const int sb = (int)stride * (int)sizeof(C);
-    return reinterpret_cast<const C*>(reinterpret_cast<const char*>(p) + (long long)a * sb);
-}
-
 // Pencil in HBM with element stride `stride`; conj() on the way in/out when isign = -1.
 template <class C>
 struct GlobalInT {
@@ -52,7 +36,7 @@ struct GlobalInT {
     long long stride;
     float isign;
     __device__ __forceinline__ C load(int a) const {
-        C t = *strided_at(p, a, stride);
+        C t = p[(long long)a * stride];
         t.y *= isign;
         return t;
     }
@@ -76,7 +60,7 @@ struct GlobalInCG {
     long long stride;
     float isign;
     __device__ __forceinline__ float2 load(int a) const {
-        float2 t = __ldcg(strided_at(p, a, stride));
+        float2 t = __ldcg(p + (long long)a * stride);
         t.y *= isign;
         return t;
     }
@@ -89,7 +73,7 @@ struct GlobalOutT {
     float isign;
     __device__ __forceinline__ void store(int a, C v) const {
         v.y *= isign;
-        *strided_at(p, a, stride) = v;
+        p[(long long)a * stride] = v;
     }
 };
 template <class C>

@@ -26,7 +26,7 @@ bool shape_pass(PassLaunch& L, int layout, int n, long long M, long long ncols, 
     L.th = (layout == LAYOUT_COL && !tc && !f64) ? th : 0;
     L.f64 = f64 ? 1 : 0;
     const long long es = f64 ? 16 : 8;  // bytes per element
-    if (M < 1 || M * es > 0x7fffffffLL) return false;  // (strides in bytes stay 32-bit: strided_at)
+    if (M < 1) return false;
     PassArgs& A = L.args;
     A.n = n;
     A.M = M;
@@ -126,7 +126,7 @@ static cudaLaunchConfig_t pair_config(const PassLaunch& L, cudaStream_t s, cudaL
 bool shape_pair(PassLaunch& L, int n, long long M, long long ncols) {
     memset(&L, 0, sizeof(L));
     pass_fn f = pair_kernel_for(n);
-    if (!f || n % 2 || M < 1 || 2 * M * (long long)sizeof(float2) > 0x7fffffffLL || ncols % M != 0) return false;
+    if (!f || n % 2 || M < 1 || ncols % M != 0) return false;
     const int n2 = n / 2;
     L.kind = PASS_AXIS;
     L.layout = LAYOUT_COL;
