@@ -19,6 +19,19 @@ namespace croft {
 template <int N>
 static pass_fn col_kernel(int w, int sv, int th) {
     constexpr int W = croft_col_width(N, 8);
+    // 24 threads per pencil (croft_col_t24): 192-thread narrow CTAs, six per SM; 384-thread
+    // 16-column CTAs, three per SM (56 registers both)
+    if (th == 24) {
+        if constexpr (croft_threads_per_pencil(N) == 32 && croft_col_t24(N, true))
+            if (w == kColNarrowWidth)
+                return sv ? croft_pass_kernel_bounded<LAYOUT_COL, N, float2, kColNarrowWidth, 6, kColNarrowWidth * 24, 1, 24>
+                          : croft_pass_kernel_bounded<LAYOUT_COL, N, float2, kColNarrowWidth, 6, kColNarrowWidth * 24, 0, 24>;
+        if constexpr (croft_threads_per_pencil(N) == 32 && croft_col_t24(N, false) && W == 16)
+            if (w == 16)
+                return sv ? croft_pass_kernel_bounded<LAYOUT_COL, N, float2, 16, 3, 16 * 24, 1, 24>
+                          : croft_pass_kernel_bounded<LAYOUT_COL, N, float2, 16, 3, 16 * 24, 0, 24>;
+        return nullptr;
+    }
     if constexpr (croft_threads_per_pencil(N) == 32 && W != kColNarrowWidth) {
         // 16 threads per pencil (32 elements each): 256-thread CTAs of 16 columns, three per SM
         if (th == 16 && w == W)

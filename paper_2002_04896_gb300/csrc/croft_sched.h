@@ -201,6 +201,19 @@ CROFT_HD constexpr int croft_col_narrow_minb(int n) { return (n == 480 || n == 4
 CROFT_HD constexpr bool croft_col_narrow(int n, int es, long long stride_bytes) {
     return es == 8 && croft_threads_per_pencil(n) == 32 && stride_bytes <= 16 * 1024;
 }
+// 24 threads per pencil instead of 32 for the complex64 column passes of some 270..512-point
+// axes (narrow: the 8-column short-stride tile; else the 16-column tile).  With 32 threads
+// the butterflies of a stage often leave lanes idle (360 = 8·9·5: 45, 40 and 72 butterflies
+// on 32 lanes use 70 % of the slots; on 24 lanes 93 %); the rule lists the lengths where 24
+// measured faster and the kernel does not spill (56 registers: six 192-thread narrow CTAs or
+// three 384-thread wide CTAs per SM).  Per-pass events, 24 vs 32 threads, y pass of
+// 512 x n x 512 / x pass of n x 512 x 512: 270 0.97 / 1.00, 288 1.09 / 1.25, 300 0.99 / 1.00,
+// 320 0.92 / 0.97, 324 0.95 / 0.93, 360 0.88 / 0.94, 384 1.05 / 0.94, 405 0.93 / 0.98 of the
+// 32-thread time (the other lengths spill at 24).
+CROFT_HD constexpr bool croft_col_t24(int n, bool narrow) {
+    if (narrow) return n == 270 || n == 320 || n == 324 || n == 360 || n == 405;
+    return n == 320 || n == 324 || n == 360 || n == 384 || n == 405;
+}
 // Column-tile width of a COL pass over a length-n axis whose elements lie stride_bytes apart.
 CROFT_HD constexpr int croft_col_width_at(int n, int es, long long stride_bytes) {
     return croft_col_narrow(n, es, stride_bytes) ? kColNarrowWidth : croft_col_width(n, es);

@@ -42,6 +42,7 @@ int main() {
             std::printf("W %d %d %d %d %d\n", n, es, croft_col_width(n, es), croft_col_width_at(n, es, 4096),
                         croft_col_width_at(n, es, 1 << 21));
         std::printf("B %d %d %d %d\n", n, croft_col_minb(n, 8), croft_pass_minb(n, 8), croft_col_narrow_minb(n));
+        std::printf("X %d %d %d\n", n, croft_col_t24(n, true) ? 1 : 0, croft_col_t24(n, false) ? 1 : 0);
     }
     return 0;
 }
@@ -58,7 +59,7 @@ def rules(tmp_path_factory):
     src.write_text(PROGRAM)
     subprocess.run([cxx, "-std=c++17", "-O1", "-I", CSRC, str(src), "-o", str(exe)], check=True)
     out = subprocess.run([str(exe)], check=True, capture_output=True, text=True).stdout
-    r = {"S": {}, "T": {}, "W": {}, "B": {}}
+    r = {"S": {}, "T": {}, "W": {}, "B": {}, "X": {}}
     for line in out.splitlines():
         tag, *v = line.split()
         v = [int(a) for a in v]
@@ -68,6 +69,8 @@ def rules(tmp_path_factory):
             r["T"][v[0]] = v[1]
         elif tag == "W":
             r["W"][(v[0], v[1])] = v[2:]
+        elif tag == "X":
+            r["X"][v[0]] = v[1:]
         else:
             r["B"][v[0]] = v[1:]
     return r
@@ -144,3 +147,24 @@ def test_launch_bounds(rules):
         assert (narrow_minb == 4) == (n in (480, 486, 500)), n
         # registers a thread may keep under the bound: 48 for five 256-thread CTAs, 64 for four
         assert 65536 // (narrow_minb * 256) >= 48
+
+
+def test_24_thread_pencils(rules):
+    # the 24-thread column kernels exist only for 32-thread lengths; their CTAs (8 or 16 columns
+    # x 24 threads) stay within the launch bound and the shared-memory budget of the tile
+    chosen = {n for n, (nar, wide) in rules["X"].items() if nar or wide}
+    assert chosen == {270, 320, 324, 360, 384, 405}
+    for n in chosen:
+        assert rules["T"][n] == 32, n
+        nar, wide = rules["X"][n]
+        w, w_short, _ = rules["W"][(n, 8)]
+        assert w == 16 and w_short == 8, n
+        for width, on in ((w_short, nar), (w, wide)):
+            if on:
+                assert width * 24 <= 512 and 24 * 20 >= n, (n, width)  # at most 20 points a thread
+                assert ((n + 1) // 2 * 2 + n * width) * 8 <= 100 * 1024, (n, width)
+        # 24 lanes use the butterfly slots of every stage at least as well as 32
+        s = rules["S"][(n, 1)]
+        def util(t):
+            return sum(n // r for r in s) / sum(-(-(n // r) // t) * t for r in s)
+        assert util(24) >= util(32) - 0.05, (n, util(24), util(32))
