@@ -85,6 +85,24 @@ def test_long_pencil_x_pass_over_wide_stride(croft_lib, dev, n):
     assert e <= tol(shape), (shape, e)
 
 
+@pytest.mark.parametrize("n", [270, 320, 324, 360, 384, 405])
+def test_24_thread_pencils_where_the_rule_takes_them(croft_lib, dev, n):
+    """The column passes of these lengths run 24 threads per pencil where the rule says so
+    (8-column y tiles of 192 threads, 16-column x tiles of 384), against the oracle with ragged
+    tiles."""
+    rng = np.random.default_rng(2400 + n)
+    for shape, axis, narrow in (((3, n, 5), "y", True), ((n, 45, 50), "x", False)):
+        x = (rng.uniform(-1, 1, shape) + 1j * rng.uniform(-1, 1, shape)).astype(np.complex64)
+        with croft_lib.Plan(*shape) as p:
+            d = _pass_desc(p.describe(), axis)
+        t24 = n in ((270, 320, 324, 360, 405) if narrow else (320, 324, 360, 384, 405))
+        want = (" T=24 W=8 block=192 " if narrow else " T=24 W=16 block=384 ") if t24 else " T=32 "
+        assert want in d, (shape, d)
+        y = run(croft_lib, x)
+        e = oracle.rel_l2(y, oracle.forward(x))
+        assert e <= tol(shape), (shape, e)
+
+
 def test_column_width_follows_the_stride(croft_lib, dev):
     """512^3: the y pass (4 KB stride) runs 8-column tiles, the x pass (2 MB stride) 16-column
     tiles split over a cluster pair of 256-thread CTAs; below 256 KB strides the plain
