@@ -253,12 +253,16 @@ static croft_status add_axis_pass(croft_plan p, int axis, int x0 = 0, int nxs = 
         th = 16;
         want_w = croft_col_width(n, 8);
     }
-    // the rules' 24-thread pencils (croft_col_t24), unless CROFT_COL_TH asked for 16
+    // the rules' 24- and 16-thread pencils (croft_col_t24, croft_col_t16), unless CROFT_COL_TH
+    // asked for 16
     if (kind < 0 && th == 0 && layout == LAYOUT_COL && !f64 && !p->axis_tc[axis] && croft_threads_per_pencil(n) == 32) {
         const int w = croft_col_width_at(n, 8, M * 8);
-        if (croft_col_t24(n, w == kColNarrowWidth)) {
+        if (croft_col_t24(n, M * 8 <= 16 * 1024)) {
             th = 24;
             want_w = w;
+        } else if (croft_col_t16(n, 8, M * 8)) {
+            th = 16;
+            want_w = croft_col_width(n, 8);
         }
     }
     if (!shape_pass(L, layout, n, M, N / n, p->axis_tc[axis] ? 1 + p->tc_prec : 0, f64, want_w, sv, th))

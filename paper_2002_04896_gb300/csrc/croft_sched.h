@@ -198,11 +198,16 @@ constexpr int kColNarrowWidth = 8;
 // of a 128 x n x 512 grid, five vs four: 480 100.3 / 98.3 us, 486 157.7 / 149.5, 500 143.4 /
 // 139.3; the other 13 lengths 0-7 % slower at four (512 110.6 / 116.7, 400 81.9 / 88.0).
 CROFT_HD constexpr int croft_col_narrow_minb(int n) { return (n == 480 || n == 486 || n == 500) ? 4 : 5; }
+// Lengths whose short-stride passes keep the 16-column tile: per-pass events on 512 x n x 512
+// (4 KB strides), 16 vs 8 columns, us: 270 206 / 219, 288 213 / 227, 300 225 / 235, 375 277 /
+// 286, 384 268 / 280, 400 286 / 295 (the other lengths 3-15 % faster with 8).
 CROFT_HD constexpr bool croft_col_narrow(int n, int es, long long stride_bytes) {
-    return es == 8 && croft_threads_per_pencil(n) == 32 && stride_bytes <= 16 * 1024;
+    return es == 8 && croft_threads_per_pencil(n) == 32 && stride_bytes <= 16 * 1024 && n != 270 && n != 288 &&
+           n != 300 && n != 375 && n != 384 && n != 400;
 }
 // 24 threads per pencil instead of 32 for the complex64 column passes of some 270..512-point
-// axes (narrow: the 8-column short-stride tile; else the 16-column tile).  With 32 threads
+// axes (short: strides of at most 16 KB, where these lengths take the 8-column tile; else the
+// 16-column tile).  With 32 threads
 // the butterflies of a stage often leave lanes idle (360 = 8·9·5: 45, 40 and 72 butterflies
 // on 32 lanes use 70 % of the slots; on 24 lanes 93 %); the rule lists the lengths where 24
 // measured faster and the kernel does not spill (56 registers: six 192-thread narrow CTAs or
@@ -210,8 +215,8 @@ CROFT_HD constexpr bool croft_col_narrow(int n, int es, long long stride_bytes) 
 // 512 x n x 512 / x pass of n x 512 x 512: 270 0.97 / 1.00, 288 1.09 / 1.25, 300 0.99 / 1.00,
 // 320 0.92 / 0.97, 324 0.95 / 0.93, 360 0.88 / 0.94, 384 1.05 / 0.94, 405 0.93 / 0.98 of the
 // 32-thread time (the other lengths spill at 24).
-CROFT_HD constexpr bool croft_col_t24(int n, bool narrow) {
-    if (narrow) return n == 270 || n == 320 || n == 324 || n == 360 || n == 405;
+CROFT_HD constexpr bool croft_col_t24(int n, bool short_stride) {
+    if (short_stride) return n == 320 || n == 324 || n == 360 || n == 405;
     return n == 320 || n == 324 || n == 360 || n == 384 || n == 405;
 }
 // Column-tile width of a COL pass over a length-n axis whose elements lie stride_bytes apart.
@@ -222,8 +227,15 @@ CROFT_HD constexpr int croft_col_width_at(int n, int es, long long stride_bytes)
 // CTAs per SM that a 256-thread pass kernel's registers must allow (0: no bound).  The
 // 256-point passes (16 threads per pencil, 16 pencils or columns per CTA) take ~50-52
 // registers unbounded - four CTAs per SM by registers; bounded to five (48 registers,
-// no spills) they keep more loads in flight.
-CROFT_HD constexpr int croft_pass_minb(int n, int es) { return (es == 8 && n == 256) ? 5 : 0; }
+// no spills) they keep more loads in flight.  So do the row passes (the z pass) of these
+// mixed-radix lengths (48-63 registers unbounded, none spilling at 48): z pass of
+// 512 x 512 x n, bounded / unbounded time: 270 0.85, 288 0.88, 300 0.87, 324 0.97, 375 0.94,
+// 400 0.95, 432 0.94, 480 0.96 (320 and 384 unchanged; 360, 405, 450, 486, 500 spill at 48).
+// The bound applies to both layouts' 256-thread kernels of these lengths; their column
+// kernels take their own bounds (croft_col_minb, croft_col_narrow_minb).
+CROFT_HD constexpr int croft_pass_minb(int n, int es) {
+    return (es == 8 && (n == 256 || n == 270 || n == 288 || n == 300 || n == 324 || n == 375 || n == 400 || n == 432 || n == 480)) ? 5 : 0;
+}
 
 // Column-tile width of the fused convolution pass: the same as a COL pass (8 columns
 // measured slower at every size from 384 to 512: 480^3 774 vs 690 us).
@@ -245,6 +257,16 @@ CROFT_HD constexpr bool croft_ring_default(int n, int es, long long stride_bytes
 // 0.217, 512x256x256 x 0.125 / 0.112; it loses below that stride (512x128x128 x 0.029 / 0.032),
 // on the 4 KB-stride y pass (512^3 y 0.400 / 0.407) and for the other even lengths (480^3 x
 // 0.348 / 0.363, 384x360x320 x 0.127 / 0.168), where the tuner can still pick it.
+// Also, from a sweep of every length (per-pass events, pair vs the rules' kernel, y pass of
+// 512 x n x 512 / x pass of n x 512 x 512, us): 486 at any stride (483 / 553, 500 / 633; its
+// plain kernel spills), 500 across 256 KB or more (549 / 629; y 532 / 516).
 CROFT_HD constexpr bool croft_pair_default(int n, int es, long long stride_bytes) {
-    return es == 8 && n == 512 && stride_bytes >= 256 * 1024;
+    return es == 8 && ((n == 512 && stride_bytes >= 256 * 1024) || n == 486 ||
+                       (n == 500 && stride_bytes >= 256 * 1024));
+}
+// Whether a column pass takes 16 threads per pencil (32 points each, the 16-column tile in
+// 256-thread CTAs) by default: 432 and 480 across 256 KB or more (x pass of n x 512 x 512:
+// 354 / 371 and 389 / 395 us against 32 threads).
+CROFT_HD constexpr bool croft_col_t16(int n, int es, long long stride_bytes) {
+    return es == 8 && (n == 432 || n == 480) && stride_bytes >= 256 * 1024;
 }

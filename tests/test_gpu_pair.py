@@ -97,3 +97,19 @@ def test_pair_default_for_512_point_long_strides(croft_lib):
     assert oracle.rel_l2(y.cpu().numpy(), ref) <= tol(x.shape)
     with croft_lib.Plan(512, 128, 128) as p:
         assert "+pair" not in p.describe()
+
+
+def test_pair_default_for_486_and_500(croft_lib):
+    """Without CROFT_PAIR: 486-point passes pair at every stride (y across 40 bytes, x across
+    18 KB), 500-point ones only across 256 KB or more."""
+    with croft_lib.Plan(486, 45, 50) as p:
+        d = p.describe()
+    assert "x:col+pair" in d, d
+    x = _noise((3, 486, 50), 21)
+    _check(croft_lib, x, 1)
+    with croft_lib.Plan(500, 256, 256) as p:
+        assert "x:col+pair" in p.describe()
+    with croft_lib.Plan(500, 45, 50) as p:
+        assert "+pair" not in p.describe()
+    with croft_lib.Plan(3, 500, 50) as p:
+        assert "+pair" not in p.describe()

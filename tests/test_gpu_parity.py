@@ -85,22 +85,32 @@ def test_long_pencil_x_pass_over_wide_stride(croft_lib, dev, n):
     assert e <= tol(shape), (shape, e)
 
 
-@pytest.mark.parametrize("n", [270, 320, 324, 360, 384, 405])
+@pytest.mark.parametrize("n", [270, 320, 324, 360, 384, 405, 432, 480])
 def test_24_thread_pencils_where_the_rule_takes_them(croft_lib, dev, n):
     """The column passes of these lengths run 24 threads per pencil where the rule says so
-    (8-column y tiles of 192 threads, 16-column x tiles of 384), against the oracle with ragged
-    tiles."""
+    (8-column y tiles of 192 threads, 16-column x tiles of 384), 32 elsewhere, against the oracle
+    with ragged tiles."""
     rng = np.random.default_rng(2400 + n)
     for shape, axis, narrow in (((3, n, 5), "y", True), ((n, 45, 50), "x", False)):
         x = (rng.uniform(-1, 1, shape) + 1j * rng.uniform(-1, 1, shape)).astype(np.complex64)
         with croft_lib.Plan(*shape) as p:
             d = _pass_desc(p.describe(), axis)
-        t24 = n in ((270, 320, 324, 360, 405) if narrow else (320, 324, 360, 384, 405))
+        t24 = n in ((320, 324, 360, 405) if narrow else (320, 324, 360, 384, 405))
         want = (" T=24 W=8 block=192 " if narrow else " T=24 W=16 block=384 ") if t24 else " T=32 "
         assert want in d, (shape, d)
         y = run(croft_lib, x)
         e = oracle.rel_l2(y, oracle.forward(x))
         assert e <= tol(shape), (shape, e)
+
+
+def test_16_thread_pencils_by_default_for_432_and_480_across_long_strides(croft_lib, dev):
+    """432- and 480-point x passes across 256 KB or more take 16 threads per pencil (16-column,
+    256-thread tiles); shorter strides keep 32 (their parity: the tuned-plan tests)."""
+    for n in (432, 480):
+        with croft_lib.Plan(n, 128, 256) as p:
+            assert " T=16 W=16 block=256 " in _pass_desc(p.describe(), "x"), p.describe()
+        with croft_lib.Plan(n, 64, 64) as p:
+            assert " T=32 " in _pass_desc(p.describe(), "x"), p.describe()
 
 
 def test_column_width_follows_the_stride(croft_lib, dev):
