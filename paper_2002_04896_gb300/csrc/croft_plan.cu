@@ -150,6 +150,7 @@ croft_status croft_plan_destroy(croft_plan plan) {
         dev_free(plan->tw_dev[a]);
         dev_free(plan->tw_pair[a]);
     }
+    dev_free(plan->tw_conv);
     for (cudaEvent_t e : plan->ev)
         if (e) cudaEventDestroy(e);
     if (plan->batch) batch_state_destroy(plan->batch);
@@ -169,6 +170,28 @@ static croft_status fail(croft_plan p, croft_status st) {
 
 // Axis pass (z: ROW; y, x: COL) of the three-pass schedule, or the x pass of the fused one.
 // Axis pass over x-planes [x0, x0 + nxs) (the whole grid unless the slab schedule asks for less).
+// Whether an axis's column passes run the tensor-copy ring kernel (croft_ring_default, a tuned
+// plan's choice, or CROFT_RING=1 / 0 for measurement).
+static bool ring_selected(croft_plan p, int axis) {
+    const int n = p->dims[axis];
+    const long long M = (axis == 2) ? 1 : (axis == 1 ? (long long)p->dims[2] : (long long)p->dims[1] * p->dims[2]);
+    if (M == 1 || p->dtype == CROFT_C2C_F64 || p->axis_tc[axis]) return false;
+    const int kind = p->axis_kind[axis];
+    const char* re = getenv("CROFT_RING");
+    return kind >= 0 ? kind == 1 : (re ? re[0] == '1' : croft_ring_default(n, 8, M * 8));
+}
+
+// The schedule variant of an axis's plain passes under the rules (croft_col_sv_default): complex64
+// column passes of 32-thread pencils only (tensor-core axes take their own schedule, the ring
+// kernel the rule's split, both from the axis's table).
+static int rules_sv(croft_plan p, int axis) {
+    const int n = p->dims[axis];
+    const long long M = (axis == 2) ? 1 : (axis == 1 ? (long long)p->dims[2] : (long long)p->dims[1] * p->dims[2]);
+    if (M == 1 || p->dtype == CROFT_C2C_F64 || p->axis_tc[axis] || croft_threads_per_pencil(n) != 32) return 0;
+    if (ring_selected(p, axis)) return 0;
+    return croft_col_sv_default(n, 8, M * 8);
+}
+
 static croft_status add_axis_pass(croft_plan p, int axis, int x0 = 0, int nxs = -1, int group = -1, int src_in = -1) {
     const int nx = nxs < 0 ? p->dims[0] : nxs, ny = p->dims[1], nz = p->dims[2];
     const long long N = (long long)nx * ny * nz;
@@ -184,9 +207,7 @@ static croft_status add_axis_pass(croft_plan p, int axis, int x0 = 0, int nxs = 
     // (croft_ring_default) or a tuned plan pick it; CROFT_RING=1 takes it for every such column
     // pass, CROFT_RING=0 for none (both for measurement).
     const int kind = p->axis_kind[axis];
-    const char* re = getenv("CROFT_RING");
-    const bool ring_pass = layout == LAYOUT_COL && !f64 && !p->axis_tc[axis] &&
-                           (kind >= 0 ? kind == 1 : (re ? re[0] == '1' : croft_ring_default(n, 8, M * 8)));
+    const bool ring_pass = layout == LAYOUT_COL && ring_selected(p, axis);
     // The cluster-pair kernel (croft_pair_kernel.cuh): tuned plans (kind 2) or CROFT_PAIR=1.
     const char* pe = getenv("CROFT_PAIR");
     const bool pair_pass = layout == LAYOUT_COL && !f64 && !p->axis_tc[axis] && !ring_pass &&
@@ -243,7 +264,7 @@ static croft_status add_axis_pass(croft_plan p, int axis, int x0 = 0, int nxs = 
         }
     }
     PassLaunch L;
-    int want_w = kind == 0 ? p->axis_w[axis] : 0, sv = kind == 0 ? p->axis_sv[axis] : 0;
+    int want_w = kind == 0 ? p->axis_w[axis] : 0, sv = kind == 0 ? p->axis_sv[axis] : rules_sv(p, axis);
     int th = kind == 0 ? p->axis_th[axis] : 0;
     // CROFT_COL_TH=16 (measurement): 16-column tiles with 16 threads per pencil for every column
     // pass of 32-thread pencils that a plan's rules would give the plain kernel
@@ -343,12 +364,14 @@ static void plan_conv(croft_plan p) {
     const long long N = (long long)p->dims[0] * p->dims[1] * p->dims[2];
     const long long M = (axis == 2) ? 1 : (axis == 1 ? (long long)p->dims[2] : (long long)p->dims[1] * p->dims[2]);
     if (f64 ? !conv64_kernel_for(n) : !conv_kernel_for(n)) return;
-    // the fused kernel runs the column schedule; the axis's twiddle table follows its pass's
+    // the fused kernel runs the column schedule; the axis's twiddle table follows its pass's,
+    // so a pass on another schedule (the rules' or a tuned radix-16-first split) gives the
+    // convolution a table of its own (complex64)
     const CroftSched sa = croft_pass_sched_v(n, Lp.layout, f64 ? 16 : 8, Lp.sv),
                      sb = croft_pass_sched(n, LAYOUT_COL, f64 ? 16 : 8);
-    if (sa.count != sb.count) return;
-    for (int i = 0; i < sa.count; ++i)
-        if (sa.r[i] != sb.r[i]) return;
+    bool same = sa.count == sb.count;
+    for (int i = 0; same && i < sa.count; ++i) same = sa.r[i] == sb.r[i];
+    if (!same && f64) return;
     PassLaunch L;
     // the kernel's column width is a compile-time constant (croft_conv_width)
     const int want_w = croft_conv_width(n, f64 ? 16 : 8);
@@ -359,6 +382,19 @@ static void plan_conv(croft_plan p) {
     L.smem = (int)smem;
     L.kind = PASS_AXIS;
     L.args.tw = p->tw_dev[axis];
+    if (!same) {
+        std::vector<float> tw(2 * (size_t)(n - 1) + 2, 0.f);
+        if (build_twiddles(n, sb.r, sb.count, tw.data()) != n - 1) return;
+        if (!p->tw_conv) {
+            if (dev_alloc((void**)&p->tw_conv, sizeof(float2) * (size_t)n) != cudaSuccess) {
+                p->tw_conv = NULL;
+                return;
+            }
+            if (cudaMemcpy(p->tw_conv, tw.data(), sizeof(float2) * (size_t)(n - 1), cudaMemcpyHostToDevice) != cudaSuccess)
+                return;
+        }
+        L.args.tw = p->tw_conv;
+    }
     L.args.tw64 = f64 ? (const double2*)p->tw_dev[axis] : nullptr;
     L.args.status = p->d_status;
     L.group = Lp.group;
@@ -422,6 +458,7 @@ static croft_status create_impl(croft_plan* out, int nx, int ny, int nz, croft_d
         p->tw_dev[a] = NULL;
         p->tw_pair[a] = NULL;
     }
+    p->tw_conv = NULL;
     p->timing = false;
     p->ev_count = 0;
     p->ngroups = 0;
@@ -475,7 +512,7 @@ static croft_status create_impl(croft_plan* out, int nx, int ny, int nz, croft_d
             // the schedule of the axis's pass (a unit element stride makes it a row pass)
             const long long M = (axis == 2) ? 1 : (axis == 1 ? (long long)nz : (long long)ny * nz);
             const CroftSched sc = croft_pass_sched_v(n, M == 1 ? LAYOUT_ROW : LAYOUT_COL, dtype == CROFT_C2C_F64 ? 16 : 8,
-                                                     p->axis_kind[axis] == 0 ? p->axis_sv[axis] : 0);
+                                                     p->axis_kind[axis] == 0 ? p->axis_sv[axis] : rules_sv(p, axis));
             ns = sc.count;
             for (int i = 0; i < ns; ++i) rad[i] = sc.r[i];
         }

@@ -24,6 +24,8 @@ struct croft_plan_s {
     std::vector<int> pass_axis;       // axis index of each pass (2 = z, 1 = y, 0 = x)
     float2* tw_dev[3];                // per-axis twiddle tables (NULL for length <= 1)
     float2* tw_pair[3];               // pair column passes: [half-length table | combine twiddles], else NULL
+    float2* tw_conv;                  // fused convolution: its axis's table in the convolution kernel's
+                                      // schedule when the axis's passes follow another one, else NULL
     bool timing;
     std::vector<cudaEvent_t> ev;      // one per logical pass + 1 (created when timing is enabled)
     int ev_count;                     // events recorded by the last exec

@@ -162,6 +162,15 @@ CROFT_HD constexpr int croft_sched_variants(int n, int layout, int es) { return 
 CROFT_HD constexpr CroftSched croft_pass_sched_v(int n, int layout, int es, int sv) {
     return croft_make_sched(n, croft_even_pow2_pass(n, layout, es) && sv == 0);
 }
+// The schedule variant the rules give a column pass (the radix-16-first split where the sweep
+// of every 32-thread length measured it faster by more than 1.5 %): 320 points at every stride
+// (16·5·4 against 8·8·5, 16-column tiles: y of 512 x 320 x 512 231 / 260 us, x of 320 x 512 x
+// 512 240 / 287), the 512-point short-stride pass (16·16·2 against 8·8·8, 8-column tiles:
+// 393 / 399).  Twiddle tables follow the pass's variant; a fused convolution on such an axis
+// gets a table of its own.
+CROFT_HD constexpr int croft_col_sv_default(int n, int es, long long stride_bytes) {
+    return (es == 8 && (n == 320 || (n == 512 && stride_bytes <= 16 * 1024))) ? 1 : 0;
+}
 
 // Column-tile width (columns per CTA) of a COL pass - a compile-time constant of
 // its kernel - for length n and complex element size es bytes: 16 columns
@@ -199,11 +208,12 @@ constexpr int kColNarrowWidth = 8;
 // 139.3; the other 13 lengths 0-7 % slower at four (512 110.6 / 116.7, 400 81.9 / 88.0).
 CROFT_HD constexpr int croft_col_narrow_minb(int n) { return (n == 480 || n == 486 || n == 500) ? 4 : 5; }
 // Lengths whose short-stride passes keep the 16-column tile: per-pass events on 512 x n x 512
-// (4 KB strides), 16 vs 8 columns, us: 270 206 / 219, 288 213 / 227, 300 225 / 235, 375 277 /
-// 286, 384 268 / 280, 400 286 / 295 (the other lengths 3-15 % faster with 8).
+// (4 KB strides), 16 vs 8 columns, us: 270 206 / 219, 288 213 / 227, 300 225 / 235, 320 231 /
+// 235 (radix-16-first split), 375 277 / 286, 384 268 / 280, 400 286 / 295 (the other lengths
+// 3-15 % faster with 8).
 CROFT_HD constexpr bool croft_col_narrow(int n, int es, long long stride_bytes) {
     return es == 8 && croft_threads_per_pencil(n) == 32 && stride_bytes <= 16 * 1024 && n != 270 && n != 288 &&
-           n != 300 && n != 375 && n != 384 && n != 400;
+           n != 300 && n != 320 && n != 375 && n != 384 && n != 400;
 }
 // 24 threads per pencil instead of 32 for the complex64 column passes of some 270..512-point
 // axes (short: strides of at most 16 KB, where these lengths take the 8-column tile; else the
@@ -216,8 +226,8 @@ CROFT_HD constexpr bool croft_col_narrow(int n, int es, long long stride_bytes) 
 // 320 0.92 / 0.97, 324 0.95 / 0.93, 360 0.88 / 0.94, 384 1.05 / 0.94, 405 0.93 / 0.98 of the
 // 32-thread time (the other lengths spill at 24).
 CROFT_HD constexpr bool croft_col_t24(int n, bool short_stride) {
-    if (short_stride) return n == 320 || n == 324 || n == 360 || n == 405;
-    return n == 320 || n == 324 || n == 360 || n == 384 || n == 405;
+    if (short_stride) return n == 324 || n == 360 || n == 405;
+    return n == 324 || n == 360 || n == 384 || n == 405;
 }
 // Column-tile width of a COL pass over a length-n axis whose elements lie stride_bytes apart.
 CROFT_HD constexpr int croft_col_width_at(int n, int es, long long stride_bytes) {

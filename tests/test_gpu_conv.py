@@ -223,3 +223,19 @@ def test_full_size_properties(croft_lib, dev, name):
     del x, g, c, y, s
     torch.cuda.empty_cache()
     assert n > 0
+
+
+@pytest.mark.parametrize("n", [320, 512])
+def test_fused_axis_on_the_radix16_first_split(croft_lib, dev, n):
+    """Axes whose passes take the radix-16-first split by the rules (320; 512 at short strides)
+    keep the fused convolution: it runs its own schedule on a twiddle table of its own."""
+    shape = (n, 2, 3)
+    with croft_lib.Plan(*shape) as p:
+        d = p.describe()
+    x_pass = d[d.index("x:"):].split(" | ")[0]
+    assert ("radix=16x5x4" if n == 320 else "radix=16x16x2") in x_pass, d
+    assert "fwd*G*bwd fused" in d, d
+    x, g = _inputs(shape, 400 + n)
+    y, _ = conv_gpu(croft_lib, x, g)
+    e = oracle.rel_l2(y, oracle.convolve(x, g))
+    assert e <= tol(shape), (shape, e)

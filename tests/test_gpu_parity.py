@@ -95,7 +95,7 @@ def test_24_thread_pencils_where_the_rule_takes_them(croft_lib, dev, n):
         x = (rng.uniform(-1, 1, shape) + 1j * rng.uniform(-1, 1, shape)).astype(np.complex64)
         with croft_lib.Plan(*shape) as p:
             d = _pass_desc(p.describe(), axis)
-        t24 = n in ((320, 324, 360, 405) if narrow else (320, 324, 360, 384, 405))
+        t24 = n in ((324, 360, 405) if narrow else (324, 360, 384, 405))
         want = (" T=24 W=8 block=192 " if narrow else " T=24 W=16 block=384 ") if t24 else " T=32 "
         assert want in d, (shape, d)
         y = run(croft_lib, x)

@@ -21,7 +21,7 @@ ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 CSRC = os.path.join(ROOT, "paper_2002_04896_gb300", "csrc")
 RADICES = {2, 3, 4, 5, 8, 9, 15, 16}
 # 32-thread lengths whose short-stride column passes keep the 16-column tile (measured faster)
-WIDE_SHORT_STRIDE = {270, 288, 300, 375, 384, 400}
+WIDE_SHORT_STRIDE = {270, 288, 300, 320, 375, 384, 400}
 
 PROGRAM = r"""
 #include <cstdio>
@@ -44,7 +44,8 @@ int main() {
             std::printf("W %d %d %d %d %d\n", n, es, croft_col_width(n, es), croft_col_width_at(n, es, 4096),
                         croft_col_width_at(n, es, 1 << 21));
         std::printf("B %d %d %d %d\n", n, croft_col_minb(n, 8), croft_pass_minb(n, 8), croft_col_narrow_minb(n));
-        std::printf("X %d %d %d\n", n, croft_col_t24(n, true) ? 1 : 0, croft_col_t24(n, false) ? 1 : 0);
+        std::printf("X %d %d %d %d %d\n", n, croft_col_t24(n, true) ? 1 : 0, croft_col_t24(n, false) ? 1 : 0,
+                    croft_col_sv_default(n, 8, 4096), croft_col_sv_default(n, 8, 1 << 21));
     }
     return 0;
 }
@@ -154,11 +155,11 @@ def test_launch_bounds(rules):
 def test_24_thread_pencils(rules):
     # the 24-thread column kernels exist only for 32-thread lengths; their CTAs (8 or 16 columns
     # x 24 threads) stay within the launch bound and the shared-memory budget of the tile
-    chosen = {n for n, (nar, wide) in rules["X"].items() if nar or wide}
-    assert chosen == {320, 324, 360, 384, 405}
+    chosen = {n for n, (nar, wide, _, _) in rules["X"].items() if nar or wide}
+    assert chosen == {324, 360, 384, 405}
     for n in chosen:
         assert rules["T"][n] == 32, n
-        nar, wide = rules["X"][n]
+        nar, wide, _, _ = rules["X"][n]
         w, w_short, _ = rules["W"][(n, 8)]
         assert w == 16 and (w_short == 8 or not nar), n  # short-stride 24-thread lengths are narrow
         for width, on in ((w_short, nar), (w, wide)):
@@ -170,3 +171,13 @@ def test_24_thread_pencils(rules):
         def util(t):
             return sum(n // r for r in s) / sum(-(-(n // r) // t) * t for r in s)
         assert util(24) >= util(32) - 0.05, (n, util(24), util(32))
+
+
+def test_radix16_first_split_by_default(rules):
+    # the rules' schedule variant: 320 points at every stride, 512 at short strides; both are
+    # 32-thread lengths whose variant kernels exist (16-column at 320, the narrow tile at 512)
+    sv = {n: tuple(v[2:]) for n, v in rules["X"].items() if v[2] or v[3]}
+    assert sv == {320: (1, 1), 512: (1, 0)}
+    for n in sv:
+        assert rules["T"][n] == 32
+    assert rules["W"][(320, 8)][1] == 16 and rules["W"][(512, 8)][1] == 8
