@@ -168,6 +168,11 @@ struct EvenPow2Sched {  // the near-equal power-of-two split (croft_pass_sched)
     __host__ __device__ static constexpr CroftSched get() { return croft_make_sched(N_, true); }
 };
 template <int N_>
+struct Mixed16Sched {  // one radix-16 stage, then the near-equal split of the rest
+    static constexpr int N = N_;
+    __host__ __device__ static constexpr CroftSched get() { return croft_make_sched_mixed(N_); }
+};
+template <int N_>
 struct Tc16Sched {
     static constexpr int N = N_;
     __host__ __device__ static constexpr CroftSched get() { return croft_make_sched_tc(N_); }

@@ -38,6 +38,10 @@ static pass_fn col_kernel(int w, int sv, int th) {
             return sv ? croft_pass_kernel_bounded<LAYOUT_COL, N, float2, W, 3, W * 16, 1, 16>
                       : croft_pass_kernel_bounded<LAYOUT_COL, N, float2, W, 3, W * 16, 0, 16>;
         if (th) return nullptr;
+        if constexpr (N == 512)
+            if (w == kColNarrowWidth && sv == 2)
+                return croft_pass_kernel_bounded<LAYOUT_COL, N, float2, kColNarrowWidth, croft_col_narrow_minb(N),
+                                                 kColNarrowWidth * 32, 2>;
         if (w == kColNarrowWidth)
             return sv ? croft_pass_kernel_bounded<LAYOUT_COL, N, float2, kColNarrowWidth, croft_col_narrow_minb(N),
                                                   kColNarrowWidth * 32, 1>

@@ -64,8 +64,11 @@ __device__ __forceinline__ void pass_body(const C* in, C* out, const PassArgs& A
         const GlobalInT<C> src{in + base, A.M, A.isign};
         const SmemColFixed<C, (WC > 0 ? WC : 1)> work{sbuf + c};
         const GlobalOutT<C> dst{out + base, A.M, A.isign};
-        // the column schedule (croft_pass_sched_v: SV = 1 is the radix-16-first variant)
-        if constexpr (SV == 0 && croft_even_pow2_pass(N, LAYOUT_COL, (int)sizeof(C)))
+        // the column schedule (croft_pass_sched_v: SV = 1 the radix-16-first variant, SV = 2 one
+        // radix-16 stage then the near-equal split)
+        if constexpr (SV == 2)
+            fft_pencil_s<Mixed16Sched<N>, T>(src, work, dst, stw, lane, ok);
+        else if constexpr (SV == 0 && croft_even_pow2_pass(N, LAYOUT_COL, (int)sizeof(C)))
             fft_pencil_s<EvenPow2Sched<N>, T>(src, work, dst, stw, lane, ok);
         else
             fft_pencil<N, T>(src, work, dst, stw, lane, ok);

@@ -159,17 +159,27 @@ CROFT_HD constexpr CroftSched croft_pass_sched(int n, int layout, int es) {
 // passes of complex64 32-thread pencils: the radix-16-first split instead of the near-equal
 // one).  croft_sched_variants(n, layout, es) is 2 for those passes, else 1.
 CROFT_HD constexpr int croft_sched_variants(int n, int layout, int es) { return croft_even_pow2_pass(n, layout, es) ? 2 : 1; }
-CROFT_HD constexpr CroftSched croft_pass_sched_v(int n, int layout, int es, int sv) {
-    return croft_make_sched(n, croft_even_pow2_pass(n, layout, es) && sv == 0);
+// Schedule variant 2: one radix-16 stage first, then the near-equal split of the rest (512 =
+// 16·8·4); a rule's choice only (croft_col_sv_default), not a tuner candidate.
+CROFT_HD constexpr CroftSched croft_make_sched_mixed(int n) {
+    CroftSched rest = croft_make_sched(n / 16, true);
+    CroftSched s{0, {0, 0, 0, 0, 0, 0, 0, 0}};
+    s.r[0] = 16;
+    for (int i = 0; i < rest.count; ++i) s.r[1 + i] = rest.r[i];
+    s.count = rest.count + 1;
+    return s;
 }
-// The schedule variant the rules give a column pass (the radix-16-first split where the sweep
-// of every 32-thread length measured it faster by more than 1.5 %): 320 points at every stride
+CROFT_HD constexpr CroftSched croft_pass_sched_v(int n, int layout, int es, int sv) {
+    return sv == 2 ? croft_make_sched_mixed(n) : croft_make_sched(n, croft_even_pow2_pass(n, layout, es) && sv == 0);
+}
+// The schedule variant the rules give a column pass (where the sweep of every 32-thread length
+// measured another split faster by more than 1.5 %): 320 points at every stride, variant 1
 // (16·5·4 against 8·8·5, 16-column tiles: y of 512 x 320 x 512 231 / 260 us, x of 320 x 512 x
-// 512 240 / 287), the 512-point short-stride pass (16·16·2 against 8·8·8, 8-column tiles:
-// 393 / 399).  Twiddle tables follow the pass's variant; a fused convolution on such an axis
-// gets a table of its own.
+// 512 240 / 287); the 512-point short-stride pass, variant 2 (16·8·4; 8-column tiles: 512^3 y
+// 387 us against 391 for 16·16·2 and 399 for 8·8·8).  Twiddle tables follow the pass's
+// variant; a fused convolution on such an axis gets a table of its own.
 CROFT_HD constexpr int croft_col_sv_default(int n, int es, long long stride_bytes) {
-    return (es == 8 && (n == 320 || (n == 512 && stride_bytes <= 16 * 1024))) ? 1 : 0;
+    return (es == 8 && n == 512 && stride_bytes <= 16 * 1024) ? 2 : ((es == 8 && n == 320) ? 1 : 0);
 }
 
 // Column-tile width (columns per CTA) of a COL pass - a compile-time constant of

@@ -233,7 +233,7 @@ def test_fused_axis_on_the_radix16_first_split(croft_lib, dev, n):
     with croft_lib.Plan(*shape) as p:
         d = p.describe()
     x_pass = d[d.index("x:"):].split(" | ")[0]
-    assert ("radix=16x5x4" if n == 320 else "radix=16x16x2") in x_pass, d
+    assert ("radix=16x5x4" if n == 320 else "radix=16x8x4") in x_pass, d
     assert "fwd*G*bwd fused" in d, d
     x, g = _inputs(shape, 400 + n)
     y, _ = conv_gpu(croft_lib, x, g)

@@ -174,10 +174,25 @@ def test_24_thread_pencils(rules):
 
 
 def test_radix16_first_split_by_default(rules):
-    # the rules' schedule variant: 320 points at every stride, 512 at short strides; both are
-    # 32-thread lengths whose variant kernels exist (16-column at 320, the narrow tile at 512)
+    # the rules' schedule variant: 320 points at every stride (16·5·4), 512 at short strides
+    # (16·8·4); both are 32-thread lengths whose variant kernels exist (16-column at 320, the
+    # narrow tile at 512)
     sv = {n: tuple(v[2:]) for n, v in rules["X"].items() if v[2] or v[3]}
-    assert sv == {320: (1, 1), 512: (1, 0)}
+    assert sv == {320: (1, 1), 512: (2, 0)}
     for n in sv:
         assert rules["T"][n] == 32
     assert rules["W"][(320, 8)][1] == 16 and rules["W"][(512, 8)][1] == 8
+
+
+def test_mixed_split_of_512(tmp_path):
+    import shutil, subprocess
+    cxx = shutil.which("g++") or shutil.which("c++")
+    if not cxx:
+        pytest.skip("no host C++ compiler")
+    src = tmp_path / "m.cpp"
+    src.write_text('#include <cstdio>\n#include "croft_sched.h"\nint main(){CroftSched s=croft_pass_sched_v(512,1,8,2);'
+                   'for(int i=0;i<s.count;++i)std::printf("%d ",s.r[i]);return 0;}\n')
+    exe = tmp_path / "m"
+    subprocess.run([cxx, "-std=c++17", "-I", CSRC, str(src), "-o", str(exe)], check=True)
+    out = subprocess.run([str(exe)], check=True, capture_output=True, text=True).stdout.split()
+    assert [int(v) for v in out] == [16, 8, 4]
