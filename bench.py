@@ -1,6 +1,6 @@
 #!/usr/bin/env python3
 """Benchmark: 3D C2C FFT (forward + backward) of a 512^3 PME-shaped complex64 grid,
-FP32 CUDA-core passes against split-precision tensor-core radix-16 stages.
+FP32 CUDA-core passes against passes with a split-precision tensor-core radix-16 stage.
 
 One step = one forward and one backward transform of the whole grid through the
 C ABI (libcroft.so), i.e. every pass of the hot path.  Metric: GFLOP/s with the
@@ -45,8 +45,8 @@ sys.path.insert(0, ROOT)
 CONFIG = "pme512"
 SHAPE = (512, 512, 512)
 WORKLOAD = ("pme512: 512x512x512 complex64 C2C forward+backward, 8M +-1 charges (net zero, iid uniform positions) "
-            "spread by order-4 B-splines, seed 4; FP32 CUDA-core passes (value) and split-precision tensor-core "
-            "radix-16 stages (tc) on the same input")
+            "spread by order-4 B-splines, seed 4; FP32 CUDA-core passes (value) and passes with a split-precision "
+            "tensor-core radix-16 stage (tc) on the same input")
 METRIC = "3D C2C FFT GFLOP/s (5N log2 N), % of HBM roofline, TC vs FP32 at fixed error"
 HBM_FALLBACK_GBS = 6800.0
 FP32_TOL_PER_LOG2 = 2e-6  # rel L2 bar of the FP32 path: 2e-6 * log2(N)

@@ -43,21 +43,22 @@ typedef struct croft_plan_s* croft_plan; /* opaque, owned by the library */
 
 typedef enum {
     CROFT_C2C_F32 = 0,           /* complex64 in/out, FP32 CUDA-core butterflies */
-    CROFT_C2C_F32_TC_BF16X3 = 1, /* complex64 in/out, radix-16 stages on tensor cores
+    CROFT_C2C_F32_TC_BF16X3 = 1, /* complex64 in/out, a radix-16 stage on tensor cores
                                     (split bf16 hi+lo operands, FP32 accumulate) */
     CROFT_C2C_F64 = 2,           /* complex128 in/out (16-byte elements), FP64 butterflies and
                                     twiddles: the paper's double complex (Sec. 5).  Axes: powers of
                                     two up to 1024 and 3, 5, 6, 10, 12, 15, 48, 60, 96, 120; three-pass
                                     schedule; single-grid plans only */
-    CROFT_C2C_F32_TC_FP16X3 = 3  /* complex64 in/out, radix-16 stages on tensor cores with split
+    CROFT_C2C_F32_TC_FP16X3 = 3  /* complex64 in/out, a radix-16 stage on tensor cores with split
                                     fp16 hi+lo operands (~22 significant bits), each butterfly
                                     scaled by a power of two into fp16's range first, FP32
                                     accumulate */
 } croft_dtype;
 /* Tensor-core dtypes (CROFT_C2C_F32_TC_*): every axis whose length has a factor 16 runs its
- * radix-16 stages as split-operand GEMMs on the tensor cores (axes of 16 .. 1024 points; a
- * longer one makes plan creation fail with CROFT_ERR_UNSUPPORTED_SIZE rather than fall back
- * to FP32); an axis without a factor 16 has no radix-16 stage and runs on the CUDA cores.
+ * first stage, a radix-16 one, as a split-operand GEMM on the tensor cores and the rest of its
+ * schedule on the CUDA cores (axes of 16 .. 1024 points; a longer one makes plan creation fail
+ * with CROFT_ERR_UNSUPPORTED_SIZE rather than fall back to FP32); an axis without a factor 16
+ * has no radix-16 stage and runs on the CUDA cores.
  * croft_plan_tc_axes reports which axes run on the tensor cores. */
 
 typedef enum {
@@ -130,7 +131,7 @@ typedef enum {
 } croft_schedule;
 
 /*
- * croft_plan_tc_axes - which axes of a single-grid plan run their radix-16 stages on the
+ * croft_plan_tc_axes - which axes of a single-grid plan run a radix-16 stage on the
  * tensor cores: bit a set for axis a (0 = x, 1 = y, 2 = z).  0 for FP32 / FP64 plans, batched
  * plans and NULL.  The library's own statement of a plan's per-axis arithmetic (the
  * precision of every result of a tensor-core plan follows from it).

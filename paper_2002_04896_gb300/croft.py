@@ -261,7 +261,7 @@ def croft_transpose_blocks(inp, out, d0: int, d1: int, block_bytes: int, stream=
 
 
 def croft_plan_tc_axes(plan: int) -> int:
-    """Bit a set when axis a (0 = x, 1 = y, 2 = z) runs its radix-16 stages on the tensor cores."""
+    """Bit a set when axis a (0 = x, 1 = y, 2 = z) runs a radix-16 stage on the tensor cores."""
     return int(_tc_axes(plan))
 
 

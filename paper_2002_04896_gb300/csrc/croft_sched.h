@@ -95,16 +95,19 @@ CROFT_HD constexpr CroftSched croft_make_sched(int n, bool even_pow2 = false) {
     return s;
 }
 
-// Schedule of the tensor-core variant: as many radix-16 stages as n has factors
-// of 16 (these run as split-bf16 GEMMs), then the ordinary schedule of the rest.
+// Schedule of the tensor-core variant: one radix-16 stage first (it runs as a split-operand
+// GEMM on the tensor cores), then the near-equal split of the rest on the CUDA cores.  One
+// tensor-core stage instead of one per factor 16: each such stage costs a GEMM round trip and
+// adds the split's rounding (512^3 forward+backward, bf16x3: 3.55 -> 3.31 ms, round trip
+// 1.12e-5 -> 7.6e-6; fp16x3 3.78 -> 3.34 ms, 2.0e-6 -> 1.1e-6).
 CROFT_HD constexpr CroftSched croft_make_sched_tc(int n) {
     CroftSched s{0, {0, 0, 0, 0, 0, 0, 0, 0}};
     int m = n, k = 0;
-    while (m > 1 && m % 16 == 0 && k < CROFT_MAX_STAGES) {
+    if (m > 1 && m % 16 == 0) {
         s.r[k++] = 16;
         m /= 16;
     }
-    const CroftSched rest = croft_make_sched(m);
+    const CroftSched rest = croft_make_sched(m, true);
     if (rest.count < 0 || k + rest.count > CROFT_MAX_STAGES) {
         s.count = -1;
         return s;

@@ -1,4 +1,4 @@
-// croft_tc_kernel.cuh - pass kernel whose radix-16 stages run on the tensor cores.
+// croft_tc_kernel.cuh - pass kernel whose first (radix-16) stage runs on the tensor cores.
 //
 // A radix-16 Stockham stage applies, to every butterfly b, the 16-point DFT
 // matrix F (F[k][j] = exp(-2 pi i jk/16)) after the twiddles: y = F u.  Over a
@@ -273,12 +273,13 @@ namespace croft {
 
 template <class SchedT, int S>
 struct TcStageInfo {
-    static constexpr bool tc = SchedT::get().r[S] == 16;
+    static constexpr bool tc = S == 0 && SchedT::get().r[S] == 16;
     static constexpr bool first = (S == 0);
     static constexpr bool last = (S == SchedT::get().count - 1);
 };
 
-// One stage with the given operands: radix-16 stages on the tensor cores, others on CUDA cores.
+// One stage with the given operands: the first (radix-16) stage on the tensor cores, the others
+// on CUDA cores.
 template <class SchedT, int S, int T, int PREC, bool GS, class Src, class Dst>
 __device__ __forceinline__ void tc_run_stage(const Src& src, const Dst& dst, const float2* stw, int lane, bool ok,
                                              const TcCtx& tc, int tc_index) {

@@ -1,4 +1,4 @@
-"""Tensor-core variants: radix-16 stages as split-operand tcgen05 GEMMs (needs a GPU).
+"""Tensor-core variants: a radix-16 stage as split-operand tcgen05 GEMMs (needs a GPU).
 
 CROFT_C2C_F32_TC_BF16X3 (bf16 hi + lo) and CROFT_C2C_F32_TC_FP16X3 (fp16 hi + lo, each
 butterfly scaled by a power of two).  Bar: relative L2 error <= 3e-5 against the FP64
