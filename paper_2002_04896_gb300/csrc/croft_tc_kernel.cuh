@@ -178,7 +178,9 @@ __device__ __forceinline__ void fft_stage_tc16(const Src& src, const Dst& dst, c
     }
     const int tid = threadIdx.x;
     const int g = tid >> 7, r = tid & 127;
-    tc_sync<GS>(g);  // every input of the stage read before the tile becomes the operand buffer
+    // every input of the stage read before the tile becomes the operand buffer (the first stage
+    // reads HBM, not the tile: no barrier)
+    if constexpr (S != 0) tc_sync<GS>(g);
 
     // fp16 operands: scale the butterfly by 2^sh so that its largest component lies in
     // [2^14, 2^15) (exact; undone on the outputs below)
