@@ -196,3 +196,43 @@ def test_mixed_split_of_512(tmp_path):
     subprocess.run([cxx, "-std=c++17", "-I", CSRC, str(src), "-o", str(exe)], check=True)
     out = subprocess.run([str(exe)], check=True, capture_output=True, text=True).stdout.split()
     assert [int(v) for v in out] == [16, 8, 4]
+
+
+def _run_snippet(tmp_path, body):
+    import shutil, subprocess
+    cxx = shutil.which("g++") or shutil.which("c++")
+    if not cxx:
+        pytest.skip("no host C++ compiler")
+    src = tmp_path / "s.cpp"
+    src.write_text('#include <cstdio>\n#include <initializer_list>\n#include "croft_sched.h"\nint main(){' + body + 'return 0;}\n')
+    exe = tmp_path / "s"
+    subprocess.run([cxx, "-std=c++17", "-I", CSRC, str(src), "-o", str(exe)], check=True)
+    return subprocess.run([str(exe)], check=True, capture_output=True, text=True).stdout
+
+
+def test_tensor_core_schedule_has_one_radix16_stage_first(tmp_path):
+    # every length <= 1024 with a factor 16: one radix-16 stage (the tensor-core one) first, then
+    # a factorisation of n / 16 into the butterfly set
+    out = _run_snippet(tmp_path, 'for(int n=16;n<=1024;n+=16){CroftSched s=croft_make_sched_tc(n);'
+                                 'std::printf("%d",n);for(int i=0;i<s.count;++i)std::printf(" %d",s.r[i]);std::printf("\\n");}')
+    for line in out.strip().splitlines():
+        n, *rs = (int(v) for v in line.split())
+        m = n
+        for p in (2, 3, 5):
+            while m % p == 0:
+                m //= p
+        if m != 1:
+            assert rs == [], (n, rs)  # not of the form 2^a 3^b 5^c: no schedule
+            continue
+        assert rs[0] == 16, (n, rs)
+        assert math.prod(rs) == n and set(rs) <= RADICES, (n, rs)
+    assert "512 16 8 4" in out and "256 16 16" in out and "1024 16 8 8" in out
+
+
+def test_pair_and_16_thread_defaults(tmp_path):
+    out = _run_snippet(tmp_path, 'for(int n : {480, 486, 500, 512, 432, 450}) for(long long sb : {4096LL, 1LL << 18, 1LL << 21})'
+                                 'std::printf("%d %lld %d %d\\n", n, sb, croft_pair_default(n, 8, sb) ? 1 : 0, croft_col_t16(n, 8, sb) ? 1 : 0);')
+    got = {(int(a), int(b)): (int(c), int(d)) for a, b, c, d in (line.split() for line in out.strip().splitlines())}
+    for (n, sb), (pair, t16) in got.items():
+        assert pair == int(n == 486 or (n in (500, 512) and sb >= 1 << 18)), (n, sb)
+        assert t16 == int(n in (432, 480) and sb >= 1 << 18), (n, sb)
